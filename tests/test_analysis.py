@@ -1,0 +1,52 @@
+"""Host-side complexity / memory models against Table 1 and Sec. IV."""
+import math
+
+import pytest
+
+from paper_2406_17981_gb300 import analysis as A
+from tests.conftest import read_golden
+
+
+def test_table1_values():
+    for d, rc, rm, rms in read_golden("table1.txt"):
+        d = int(d)
+        # printed to two decimals, halves rounded up (65/8 = 8.125 -> 8.13)
+        assert abs(A.ratio_complexity_asymptotic(d) - float(rc)) <= 0.005 + 1e-12
+        assert abs(A.ratio_memory(d) - float(rm)) <= 0.005 + 1e-12
+        assert abs(A.ratio_memory_sym(d) - float(rms)) <= 0.005 + 1e-12
+
+
+def test_outlook_d3_fractions():
+    want = {r[0]: int(r[1]) / int(r[2]) for r in read_golden("outlook_d3.txt")}
+    assert A.ratio_complexity_asymptotic(3) == pytest.approx(want["R_c"], rel=1e-15)
+    assert A.ratio_memory(3) == pytest.approx(want["R_m"], rel=1e-15)
+    assert A.ratio_memory_sym(3) == pytest.approx(want["R_m_sym"], rel=1e-15)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 6])
+def test_compratio_lines_agree_and_converge(d):
+    # the first line of Eq. CompRatio (C_embed / C_split) equals the second
+    for n in (2, 16, 1024):
+        assert A.complexity_embed(d, n) / A.complexity_split(d, n) == pytest.approx(
+            A.ratio_complexity(d, n), rel=1e-12)
+    big = 2 ** 200
+    assert A.ratio_complexity(d, big) == pytest.approx(A.ratio_complexity_asymptotic(d), rel=0.01)
+    assert A.ratio_complexity_printed(d, big) == pytest.approx(A.ratio_complexity_asymptotic(d), rel=0.01)
+
+
+def test_block_memory_ratio_reduces_to_paper():
+    for d in range(2, 7):
+        # c = 1, full symbol 2^d s on both sides: Eq. MemRatio
+        assert A.ratio_memory_blocks(d, 1, 2 ** d, 2 ** d) == pytest.approx(A.ratio_memory(d))
+        # c = 1, symbol stored in s elements on both sides: Eq. MemRatioSym
+        assert A.ratio_memory_blocks(d, 1, 1, 1) == pytest.approx(A.ratio_memory_sym(d))
+
+
+def test_split_traffic_model_d3():
+    V = A.vector_bytes((8, 8, 8), 3, 1, 8)
+    b = A.split_pass_bytes((8, 8, 8), 3, 1, 8, 0)
+    assert b["total"] == 26 * V
+    V2 = A.vector_bytes((8, 8), 1, 1, 8)
+    assert A.split_pass_bytes((8, 8), 1, 1, 8, 0)["total"] == 10 * V2
+    V1 = A.vector_bytes((8,), 1, 1, 8)
+    assert A.split_pass_bytes((8,), 1, 1, 8, 0)["total"] == 2 * V1
