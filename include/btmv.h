@@ -1,0 +1,221 @@
+/*
+ * btmv.h -- d-level block Toeplitz matrix-vector product y = T x on one GPU,
+ *           by the lazy-embedding / eager-projection split FFT of
+ *           Siron & Molesky, "A Split Fast Fourier Transform Algorithm for
+ *           Block Toeplitz Matrix-Vector Multiplication" (arXiv 2406.17981).
+ *
+ * The operation (Sec. I, "extending the diagonal bands"): T has d levels of
+ * Toeplitz structure with c x c blocks generated by t_ab[p],
+ * p_m in [-(n_m - 1), n_m - 1]; block (i, j) holds t[i - j], so
+ *
+ *     y_a[i] = sum_b sum_j t_ab[i - j] x_b[j],   i, j in [0,n_1) x ... x [0,n_d).
+ *
+ * The split method (Sec. II.A-B, Algorithm 1) never forms the 2^d-times larger
+ * circulant embedding: along each level the doubled transform is computed as
+ * its even half FFT_n(v) and its odd half FFT_n(P v), P[k] = exp(-i pi k/n),
+ * recursively; each leaf multiplies by its 2^-d part S_b[l] = S[2l + b] of
+ * the transformed embedded generator, and the halves are
+ * merged back as v_even + conj(P) v_odd right after each inverse transform.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are interleaved (re, im): float2 for BTMV_C64, double2
+ *   for BTMV_C128.  Generators are always given in double precision.
+ * - Vectors x and y are laid out [nrhs][c][n_1]...[n_d], last index fastest,
+ *   contiguous, 16-byte aligned.  They may be device pointers (cudaMalloc,
+ *   torch tensors) or host pointers (pinned or pageable); host pointers are
+ *   staged through device buffers owned by the plan.
+ * - Streams are passed as void* (a cudaStream_t; NULL is the legacy default
+ *   stream).  Work on device pointers is enqueued asynchronously.
+ * - Every call returns a btmv_status.  On failure, btmv_last_error() gives
+ *   a message for the calling thread.  Asynchronous device errors surface on
+ *   the next call that synchronises or checks the stream.
+ * - A plan may be used by one stream at a time.
+ */
+#ifndef BTMV_H
+#define BTMV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BTMV_API __attribute__((visibility("default")))
+#else
+#define BTMV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct btmv_plan_s* btmv_plan;
+
+typedef enum {
+  BTMV_OK = 0,
+  BTMV_E_ARG = 1,          /* invalid argument (null, size, alias, layout) */
+  BTMV_E_NOMEM = 2,        /* device or host allocation failed             */
+  BTMV_E_CUDA = 3,         /* a CUDA runtime call or kernel launch failed  */
+  BTMV_E_STATE = 4,        /* call out of order (apply before set_kernel)  */
+  BTMV_E_UNSUPPORTED = 5,  /* size / combination not supported             */
+  BTMV_E_TIMEOUT = 6       /* a bounded device-side wait expired           */
+} btmv_status;
+
+/* precision of vectors, symbol and arithmetic */
+enum { BTMV_C64 = 0, BTMV_C128 = 1 };
+
+/* algorithm */
+enum {
+  BTMV_ALGO_SPLIT = 0,     /* Algorithm 1: lazy embedding, eager projection      */
+  BTMV_ALGO_FULL = 1       /* plain full 2^d circulant embedding (Sec. I), own
+                              kernels; for comparison                          */
+};
+
+/* symmetry flags for btmv_set_kernel (may be OR-ed) */
+enum {
+  BTMV_SYM_NONE = 0,
+  BTMV_SYM_BLOCK = 1,      /* t_ab = t_ba: only blocks a <= b are read/stored   */
+  BTMV_SYM_PARITY = 2      /* per-(block, dim) parity t(-p_m) = +-t(p_m): the
+                              generator is given on the non-negative orthant and
+                              the symbol is stored mirror-compressed (Sec. II.C) */
+};
+
+/* plan flags for btmv_plan_create (may be OR-ed) */
+enum {
+  BTMV_FLAG_NONE = 0,
+  BTMV_FLAG_PROFILE = 1u << 0  /* record a CUDA event pair around every kernel
+                                  launch of btmv_apply (see btmv_profile_read) */
+};
+
+/*
+ * btmv_plan_create -- allocate a plan for one problem geometry.
+ *   out       [out] receives the plan handle (host pointer).
+ *   d         number of Toeplitz levels, 1 <= d <= 4.
+ *   n         host array of d level sizes, n[m] >= 1; every n[m] must factor
+ *             into 2, 3, 5 and 7 and n[m] <= 1024 (BTMV_ALGO_FULL: 2 n[m] <= 2048).
+ *   c         block size (components), 1 <= c <= 3.
+ *   precision BTMV_C64 or BTMV_C128.
+ *   algo      BTMV_ALGO_SPLIT or BTMV_ALGO_FULL.
+ *   max_rhs   largest nrhs later passed to btmv_apply (>= 1).
+ *   flags     BTMV_FLAG_*.
+ * Allocates the twiddle tables and the workspace: (d - 1) vectors of
+ * max_rhs * c * prod(n) complex for SPLIT (the paper's (d+1)-vector peak with
+ * x and y, Sec. II.C), 2^d such vectors for FULL.  The device is the current
+ * CUDA device.  Errors: BTMV_E_ARG, BTMV_E_UNSUPPORTED, BTMV_E_NOMEM, BTMV_E_CUDA.
+ */
+BTMV_API btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n, int c,
+                             int precision, int algo, int max_rhs, uint32_t flags);
+
+/*
+ * btmv_set_kernel -- set the generating coefficients (one-time symbol build).
+ *   t         host, complex128 interleaved (2 doubles per value):
+ *             without BTMV_SYM_PARITY: [c][c][2n_1 - 1]...[2n_d - 1], offset p_m
+ *               stored at index p_m + n_m - 1;
+ *             with BTMV_SYM_PARITY: [c][c][n_1]...[n_d], offsets p_m >= 0 only.
+ *             With BTMV_SYM_BLOCK only blocks a <= b are read.
+ *   sym_flags BTMV_SYM_*.
+ *   parity    host int8 [c][c][d] of +1 / -1 (t(.., -p_m, ..) = parity * t(.., p_m, ..)),
+ *             required with BTMV_SYM_PARITY, else ignored (may be NULL).  A -1
+ *             entry requires t = 0 on the plane p_m = 0 of that block.
+ *   stream    stream for the build; the call synchronises it before returning.
+ * Computes, in FP64 on the device, every leaf part S_b = DFT_n(P_b (c~_lo +
+ * (-1)^b c~_hi)) / prod(2 n_m) of the transformed embedded generator
+ * (Sec. I embedding with free entry s0 = 0; Sec. II.C split into 2^d parts)
+ * and rounds it once to the plan precision.  Storage: full, 2^d prod(n) values
+ * per stored block; or with BTMV_SYM_PARITY (split algo only) the mirror-
+ * compressed prod(n_m + 1) values per stored block (Sec. II.C symmetric /
+ * skew-symmetric storage).  May be called again to replace the generator.
+ * Errors: BTMV_E_ARG, BTMV_E_NOMEM, BTMV_E_CUDA.
+ */
+BTMV_API btmv_status btmv_set_kernel(btmv_plan p, const double* t, uint32_t sym_flags,
+                            const int8_t* parity, void* stream);
+
+/*
+ * btmv_apply -- y = T x for nrhs right-hand sides.
+ *   x, y      [nrhs][c][n_1]..[n_d] complex (plan precision); device or host
+ *             pointers; must not overlap.  x is read only, y is overwritten.
+ *   nrhs      0 <= nrhs <= max_rhs (0 is a no-op).
+ *   stream    work is enqueued on it; with host pointers the call copies
+ *             through plan-owned device buffers and synchronises the stream.
+ * SPLIT: depth-first traversal of Algorithm 1 -- forward split passes along
+ * levels 1..d-1, a fused leaf pass along level d (both halves, symbol
+ * multiply, merge), merge passes back up; peak (d+1) vectors.
+ * Errors: BTMV_E_ARG, BTMV_E_STATE (no generator set), BTMV_E_CUDA.
+ */
+BTMV_API btmv_status btmv_apply(btmv_plan p, const void* x, void* y, int nrhs, void* stream);
+
+/*
+ * btmv_apply_batched -- y_k = T_k x_k for count independent plans, enqueued
+ * as one unit of work on stream.
+ *   plans, x, y, nrhs  host arrays of length count; entry k as in btmv_apply
+ *                      (device pointers only).  Plans must be distinct.
+ * Errors: as btmv_apply; on an argument error nothing is enqueued.
+ */
+BTMV_API btmv_status btmv_apply_batched(int count, const btmv_plan* plans, const void* const* x,
+                               void* const* y, const int* nrhs, void* stream);
+
+/* btmv_destroy -- free every device and host resource of the plan (NULL ok).
+ * Synchronises the device work of the plan first. */
+BTMV_API btmv_status btmv_destroy(btmv_plan p);
+
+/* btmv_last_error -- message of the last failure on this thread ("" if none).
+ * The pointer stays valid until the next btmv call on this thread. */
+BTMV_API const char* btmv_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Introspection (tests, benchmarks, serving admission)
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int d, c, precision, algo, max_rhs;
+  int n[4];
+  int nsym;                 /* stored symbol blocks: c*c, or c(c+1)/2 with BTMV_SYM_BLOCK */
+  int compressed;           /* 1 if the mirror-compressed parity store is in use */
+  int has_symbol;
+  int launches_per_apply;   /* kernel launches of one btmv_apply (device pointers) */
+  size_t symbol_bytes;      /* device bytes of the symbol store */
+  size_t workspace_bytes;   /* device bytes of the workspace vectors */
+  size_t table_bytes;       /* device bytes of twiddle tables */
+  size_t vector_bytes;      /* bytes of one vector at nrhs = 1 */
+} btmv_plan_info_t;
+
+/* btmv_plan_get_info -- fill *info (host pointer).  Errors: BTMV_E_ARG. */
+BTMV_API btmv_status btmv_plan_get_info(btmv_plan p, btmv_plan_info_t* info);
+
+/*
+ * btmv_get_symbol -- copy the device symbol store to host memory `out`
+ * (bytes >= info.symbol_bytes), synchronously.  Layout: 2^d parity classes
+ * b = (b_1..b_d) in order sum_m b_m 2^(d-m) (b_1 most significant); class b
+ * holds nsym blocks, each a row-major box of J_1(b_1) x .. x J_d(b_d) values
+ * S[2 j + b] (j_m < J_m).  Full store: J_m = n_m.  Compressed store:
+ * J_m(b_m) = floor((n_m - b_m)/2) + 1 (the frequencies f <= n_m; the others
+ * follow from S[2n - f] = +-S[f]).  Stored block order: c = 1: (0,0); c = 3
+ * with BTMV_SYM_BLOCK: (0,0),(1,1),(2,2),(0,1),(0,2),(1,2); otherwise
+ * row-major (a, b).  Errors: BTMV_E_ARG, BTMV_E_STATE, BTMV_E_CUDA.
+ */
+BTMV_API btmv_status btmv_get_symbol(btmv_plan p, void* out, size_t bytes);
+
+/* kernel kinds reported by btmv_profile_read */
+enum {
+  BTMV_K_FWD_SPLIT = 0,    /* forward split pass (levels 1..d-1)              */
+  BTMV_K_LEAF = 1,         /* fused leaf pass (level d)                        */
+  BTMV_K_MERGE = 2,        /* backward merge pass (levels d-1..1)              */
+  BTMV_K_FULL_FWD = 3,     /* full embedding: forward passes on the 2n grid    */
+  BTMV_K_FULL_LEAF = 4,    /* full embedding: last-dim forward+multiply+inverse */
+  BTMV_K_FULL_INV = 5,     /* full embedding: inverse passes (+ projection)    */
+  BTMV_K_COPY = 6,         /* host staging copies                              */
+  BTMV_K_NKINDS = 7
+};
+
+/*
+ * btmv_profile_read -- with BTMV_FLAG_PROFILE, synchronise the events
+ * recorded since the last read and return per-kernel-kind totals.
+ *   ms_total  host double[BTMV_K_NKINDS]: summed event-measured milliseconds.
+ *   launches  host int64[BTMV_K_NKINDS]: launch counts.
+ * Resets the accumulators.  Errors: BTMV_E_ARG, BTMV_E_STATE (flag not set),
+ * BTMV_E_CUDA.
+ */
+BTMV_API btmv_status btmv_profile_read(btmv_plan p, double* ms_total, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BTMV_H */

@@ -1,0 +1,781 @@
+// C ABI of libbtmv: plans, the one-time FP64 symbol build, and the
+// depth-first schedule of Algorithm 1 (split) or the plain full embedding.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/btmv.h"
+#include "kernels.cuh"
+
+using namespace btmv;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+static btmv_status fail(btmv_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CUDA_TRY(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? BTMV_E_NOMEM : BTMV_E_CUDA,          \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+// ------------------------------------------------------------------ plan
+struct TableSet {
+  void* mem = nullptr;                 // device
+  std::map<int, size_t> off_f, off_d;  // N -> byte offset of [tw N][ph N]
+  size_t bytes = 0;
+};
+
+struct btmv_plan_s {
+  int d = 0, c = 0, prec = 0, algo = 0, max_rhs = 0;
+  uint32_t flags = 0;
+  int n[MAX_D] = {1, 1, 1, 1};
+  long long s = 1;          // prod n
+  long long s2 = 1;         // prod 2n
+  size_t esz = 8;           // bytes per complex
+  int dev = 0;
+  TableSet tab;
+  FftDev fft_apply[MAX_D];  // per dim, plan precision (N = n_m split, 2 n_m full)
+  FftDev fft_sym[MAX_D];    // per dim, FP64, N = n_m
+  // symbol
+  void* sym = nullptr;
+  size_t sym_bytes = 0;
+  SymDev symdev;
+  bool has_sym = false;
+  int nsym = 0;
+  int compressed = 0;
+  // workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  std::vector<void*> W;     // split: d-1 vectors; full: Z
+  // host staging
+  void* stage_x = nullptr;
+  void* stage_y = nullptr;
+  // profiling
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  double acc_ms[BTMV_K_NKINDS] = {0};
+  int64_t acc_n[BTMV_K_NKINDS] = {0};
+  int launches = 0;
+};
+
+static bool factor_radices(int N, FftDev& f) {
+  f.N = N;
+  f.nst = 0;
+  int a = 0, m = N;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  int c3 = 0, c5 = 0, c7 = 0;
+  while (m % 3 == 0) { m /= 3; ++c3; }
+  while (m % 5 == 0) { m /= 5; ++c5; }
+  while (m % 7 == 0) { m /= 7; ++c7; }
+  if (m != 1) return false;
+  std::vector<int> r;
+  while (a >= 4) {
+    if (a == 5) { r.push_back(8); r.push_back(4); a = 0; break; }
+    r.push_back(16);
+    a -= 4;
+  }
+  if (a == 3) r.push_back(8);
+  if (a == 2) r.push_back(4);
+  if (a == 1) r.push_back(2);
+  for (int i = 0; i < c7; ++i) r.push_back(7);
+  for (int i = 0; i < c5; ++i) r.push_back(5);
+  for (int i = 0; i < c3; ++i) r.push_back(3);
+  if ((int)r.size() > MAX_STAGES) return false;
+  for (size_t i = 0; i < r.size(); ++i) f.rad[i] = r[i];
+  f.nst = (int)r.size();
+  return true;
+}
+
+// exp(-2 pi i k / N) and exp(-i pi k / N) in extended precision, rounded once.
+static void fill_tables(int N, std::vector<long double>& twc, std::vector<long double>& tws,
+                        std::vector<long double>& phc, std::vector<long double>& phs) {
+  const long double PI = 3.141592653589793238462643383279502884L;
+  twc.resize(N); tws.resize(N); phc.resize(N); phs.resize(N);
+  for (int k = 0; k < N; ++k) {
+    const long double t = 2.0L * PI * (long double)k / (long double)N;
+    twc[k] = cosl(t); tws[k] = -sinl(t);
+    const long double p = PI * (long double)k / (long double)N;
+    phc[k] = cosl(p); phs[k] = -sinl(p);
+  }
+}
+
+static btmv_status build_tables(btmv_plan p, const std::vector<int>& Nf, const std::vector<int>& Nd) {
+  std::map<int, int> uf, ud;
+  for (int N : Nf) uf[N] = 1;
+  for (int N : Nd) ud[N] = 1;
+  size_t off = 0;
+  for (auto& kv : uf) { p->tab.off_f[kv.first] = off; off += (size_t)2 * kv.first * sizeof(float2); off = (off + 255) / 256 * 256; }
+  for (auto& kv : ud) { p->tab.off_d[kv.first] = off; off += (size_t)2 * kv.first * sizeof(double2); off = (off + 255) / 256 * 256; }
+  p->tab.bytes = off;
+  std::vector<unsigned char> host(off, 0);
+  std::vector<long double> a, b, c, d;
+  for (auto& kv : p->tab.off_f) {
+    const int N = kv.first;
+    fill_tables(N, a, b, c, d);
+    float2* t = (float2*)(host.data() + kv.second);
+    for (int k = 0; k < N; ++k) { t[k] = make_float2((float)a[k], (float)b[k]); t[N + k] = make_float2((float)c[k], (float)d[k]); }
+  }
+  for (auto& kv : p->tab.off_d) {
+    const int N = kv.first;
+    fill_tables(N, a, b, c, d);
+    double2* t = (double2*)(host.data() + kv.second);
+    for (int k = 0; k < N; ++k) { t[k] = make_double2((double)a[k], (double)b[k]); t[N + k] = make_double2((double)c[k], (double)d[k]); }
+  }
+  CUDA_TRY(cudaMalloc(&p->tab.mem, off));
+  CUDA_TRY(cudaMemcpy(p->tab.mem, host.data(), off, cudaMemcpyHostToDevice));
+  return BTMV_OK;
+}
+
+static void set_fft(btmv_plan p, FftDev& f, int N, bool dbl) {
+  factor_radices(N, f);
+  const size_t off = dbl ? p->tab.off_d[N] : p->tab.off_f[N];
+  const size_t esz = dbl ? sizeof(double2) : sizeof(float2);
+  f.tw = (const unsigned char*)p->tab.mem + off;
+  f.ph = (const unsigned char*)p->tab.mem + off + (size_t)N * esz;
+}
+
+static void free_plan(btmv_plan p) {
+  if (!p) return;
+  for (auto& r : p->pending) { p->pool.push_back(r.a); p->pool.push_back(r.b); }
+  for (auto e : p->pool) cudaEventDestroy(e);
+  if (p->tab.mem) cudaFree(p->tab.mem);
+  if (p->sym) cudaFree(p->sym);
+  if (p->ws) cudaFree(p->ws);
+  if (p->stage_x) cudaFree(p->stage_x);
+  if (p->stage_y) cudaFree(p->stage_y);
+  delete p;
+}
+
+extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n, int c, int precision,
+                                        int algo, int max_rhs, uint32_t flags) {
+  g_err.clear();
+  if (!out) return fail(BTMV_E_ARG, "plan_create: out is NULL");
+  *out = nullptr;
+  if (d < 1 || d > MAX_D) return fail(BTMV_E_ARG, "plan_create: d=%d outside [1,%d]", d, MAX_D);
+  if (!n) return fail(BTMV_E_ARG, "plan_create: n is NULL");
+  if (c < 1 || c > 3) return fail(BTMV_E_ARG, "plan_create: c=%d outside [1,3]", c);
+  if (precision != BTMV_C64 && precision != BTMV_C128) return fail(BTMV_E_ARG, "plan_create: bad precision %d", precision);
+  if (algo != BTMV_ALGO_SPLIT && algo != BTMV_ALGO_FULL) return fail(BTMV_E_ARG, "plan_create: bad algo %d", algo);
+  if (max_rhs < 1) return fail(BTMV_E_ARG, "plan_create: max_rhs=%d < 1", max_rhs);
+  if (flags & ~(uint32_t)BTMV_FLAG_PROFILE) return fail(BTMV_E_ARG, "plan_create: unknown flags 0x%x", flags);
+  for (int m = 0; m < d; ++m) {
+    if (n[m] < 1) return fail(BTMV_E_ARG, "plan_create: n[%d]=%d < 1", m, n[m]);
+    const int N = algo == BTMV_ALGO_FULL ? 2 * n[m] : n[m];
+    FftDev f;
+    if (n[m] > 1024 || !factor_radices(N, f))
+      return fail(BTMV_E_UNSUPPORTED, "plan_create: n[%d]=%d must be <= 1024 and 7-smooth", m, n[m]);
+  }
+  btmv_plan p = new btmv_plan_s();
+  p->d = d; p->c = c; p->prec = precision; p->algo = algo; p->max_rhs = max_rhs; p->flags = flags;
+  p->esz = precision == BTMV_C64 ? sizeof(float2) : sizeof(double2);
+  for (int m = 0; m < d; ++m) { p->n[m] = n[m]; p->s *= n[m]; p->s2 *= 2 * n[m]; }
+  if (cudaGetDevice(&p->dev) != cudaSuccess) { free_plan(p); return fail(BTMV_E_CUDA, "plan_create: no CUDA device"); }
+
+  std::vector<int> Nf, Nd;
+  for (int m = 0; m < d; ++m) {
+    const int N = algo == BTMV_ALGO_FULL ? 2 * n[m] : n[m];
+    if (precision == BTMV_C64) Nf.push_back(N); else Nd.push_back(N);
+    Nd.push_back(n[m]);  // FP64 symbol build
+  }
+  btmv_status st = build_tables(p, Nf, Nd);
+  if (st != BTMV_OK) { free_plan(p); return st; }
+  for (int m = 0; m < d; ++m) {
+    const int N = algo == BTMV_ALGO_FULL ? 2 * n[m] : n[m];
+    set_fft(p, p->fft_apply[m], N, precision == BTMV_C128);
+    set_fft(p, p->fft_sym[m], n[m], true);
+  }
+  const size_t V = (size_t)max_rhs * c * p->s * p->esz;
+  size_t nvec = 0;
+  if (algo == BTMV_ALGO_SPLIT) nvec = (size_t)(d - 1);
+  p->ws_bytes = algo == BTMV_ALGO_SPLIT ? nvec * V : (size_t)max_rhs * c * p->s2 * p->esz;
+  if (p->ws_bytes) {
+    cudaError_t e = cudaMalloc(&p->ws, p->ws_bytes);
+    if (e != cudaSuccess) { free_plan(p); return fail(BTMV_E_NOMEM, "plan_create: workspace of %zu bytes: %s", p->ws_bytes, cudaGetErrorString(e)); }
+    if (algo == BTMV_ALGO_SPLIT)
+      for (size_t i = 0; i < nvec; ++i) p->W.push_back((unsigned char*)p->ws + i * V);
+    else
+      p->W.push_back(p->ws);
+  }
+  *out = p;
+  return BTMV_OK;
+}
+
+// --------------------------------------------------------- symbol build
+static int block_index(int c, bool bsym, int a, int b) {
+  if (!bsym) return a * c + b;
+  if (a == b) return a;
+  if (a > b) { int t = a; a = b; b = t; }
+  // upper triangle after the c diagonal blocks, row-major
+  int k = c;
+  for (int i = 0; i < c; ++i)
+    for (int j = i + 1; j < c; ++j) {
+      if (i == a && j == b) return k;
+      ++k;
+    }
+  return -1;
+}
+
+extern "C" btmv_status btmv_set_kernel(btmv_plan p, const double* t, uint32_t sym_flags, const int8_t* parity,
+                                       void* stream) {
+  g_err.clear();
+  if (!p) return fail(BTMV_E_ARG, "set_kernel: plan is NULL");
+  if (!t) return fail(BTMV_E_ARG, "set_kernel: t is NULL");
+  if (sym_flags & ~(uint32_t)(BTMV_SYM_BLOCK | BTMV_SYM_PARITY)) return fail(BTMV_E_ARG, "set_kernel: unknown sym flags 0x%x", sym_flags);
+  const bool bsym = (sym_flags & BTMV_SYM_BLOCK) != 0;
+  const bool par = (sym_flags & BTMV_SYM_PARITY) != 0;
+  const int d = p->d, c = p->c;
+  if (par && !parity) return fail(BTMV_E_ARG, "set_kernel: BTMV_SYM_PARITY needs a parity array");
+  if (par) {
+    for (int a = 0; a < c; ++a)
+      for (int b = 0; b < c; ++b)
+        for (int m = 0; m < d; ++m) {
+          const int8_t v = parity[(a * c + b) * d + m];
+          if (v != 1 && v != -1) return fail(BTMV_E_ARG, "set_kernel: parity[%d][%d][%d]=%d not +-1", a, b, m, v);
+          if (bsym && v != parity[(b * c + a) * d + m]) return fail(BTMV_E_ARG, "set_kernel: BTMV_SYM_BLOCK with asymmetric parity");
+        }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nsym = bsym ? c * (c + 1) / 2 : c * c;
+  const int compressed = (par && p->algo == BTMV_ALGO_SPLIT) ? 1 : 0;
+
+  // class geometry
+  SymDev sd;
+  memset(&sd, 0, sizeof sd);
+  sd.d = d; sd.nsym = nsym; sd.compressed = compressed;
+  for (int m = 0; m < d; ++m) sd.n[m] = p->n[m];
+  long long off = 0;
+  const int ncls = 1 << d;
+  for (int cls = 0; cls < ncls; ++cls) {
+    long long blk = 1;
+    for (int m = 0; m < d; ++m) {
+      const int bm = (cls >> (d - 1 - m)) & 1;
+      const int J = compressed ? (p->n[m] - bm) / 2 + 1 : p->n[m];
+      sd.J[cls][m] = J;
+      blk *= J;
+    }
+    sd.cls_off[cls] = off;
+    sd.blk[cls] = blk;
+    off += blk * nsym;
+  }
+  const size_t store_bytes = (size_t)off * p->esz;
+  int pairs[9][2];
+  for (int a = 0; a < c; ++a)
+    for (int b = 0; b < c; ++b) {
+      const int k = block_index(c, bsym, a, b);
+      sd.comp[a][b] = k;
+      if (!bsym || a <= b) { pairs[k][0] = a; pairs[k][1] = b; }
+    }
+  for (int k = 0; k < nsym; ++k) {
+    int mask = 0;
+    if (par)
+      for (int m = 0; m < d; ++m)
+        if (parity[(pairs[k][0] * c + pairs[k][1]) * d + m] < 0) mask |= 1 << m;
+    sd.oddmask[k] = mask;
+  }
+
+  // device copy of t (only the needed blocks are used)
+  long long tb = 1;
+  for (int m = 0; m < d; ++m) tb *= par ? p->n[m] : (2 * p->n[m] - 1);
+  const size_t t_bytes = (size_t)c * c * tb * sizeof(double2);
+  void* t_dev = nullptr;
+  void* F = nullptr;
+  void* store = p->sym;
+  if (p->sym && p->sym_bytes != store_bytes) { cudaFree(p->sym); p->sym = nullptr; store = nullptr; p->has_sym = false; }
+  cudaError_t e = cudaMalloc(&t_dev, t_bytes);
+  if (e != cudaSuccess) return fail(BTMV_E_NOMEM, "set_kernel: %zu bytes for t: %s", t_bytes, cudaGetErrorString(e));
+  e = cudaMalloc(&F, (size_t)nsym * p->s * sizeof(double2));
+  if (e != cudaSuccess) { cudaFree(t_dev); return fail(BTMV_E_NOMEM, "set_kernel: FP64 work buffer: %s", cudaGetErrorString(e)); }
+  if (!store) {
+    e = cudaMalloc(&store, store_bytes);
+    if (e != cudaSuccess) { cudaFree(t_dev); cudaFree(F); return fail(BTMV_E_NOMEM, "set_kernel: symbol store of %zu bytes: %s", store_bytes, cudaGetErrorString(e)); }
+  }
+  btmv_status ret = BTMV_OK;
+  auto bail = [&](btmv_status s2, const char* what, cudaError_t ce) {
+    ret = fail(s2, "set_kernel: %s: %s", what, cudaGetErrorString(ce));
+  };
+  e = cudaMemcpyAsync(t_dev, t, t_bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) bail(BTMV_E_CUDA, "copy of t", e);
+
+  FoldArgs fa;
+  memset(&fa, 0, sizeof fa);
+  fa.F = (double2*)F; fa.t = (const double2*)t_dev; fa.d = d; fa.c = c; fa.nsym = nsym;
+  fa.parity_layout = par ? 1 : 0; fa.s = p->s;
+  double scale = 1.0;
+  for (int m = 0; m < d; ++m) { fa.n[m] = p->n[m]; scale /= (2.0 * p->n[m]); }
+  fa.scale = scale;
+  for (int k = 0; k < nsym; ++k) { fa.pairs[k][0] = pairs[k][0]; fa.pairs[k][1] = pairs[k][1]; }
+  if (par)
+    for (int a = 0; a < c; ++a)
+      for (int b = 0; b < c; ++b)
+        for (int m = 0; m < d; ++m) fa.par[a][b][m] = parity[(a * c + b) * d + m];
+
+  for (int cls = 0; cls < ncls && ret == BTMV_OK; ++cls) {
+    for (int m = 0; m < d; ++m) fa.cls_bits[m] = (cls >> (d - 1 - m)) & 1;
+    if ((e = launch_fold(fa, st)) != cudaSuccess) { bail(BTMV_E_CUDA, "fold kernel", e); break; }
+    // FP64 forward transforms along every dim, P_{b_m}-twiddled, in place
+    for (int m = 0; m < d && ret == BTMV_OK; ++m) {
+      long long outer = nsym, inner = 1;
+      for (int q = 0; q < m; ++q) outer *= p->n[q];
+      for (int q = m + 1; q < d; ++q) inner *= p->n[q];
+      PassArgs pa;
+      memset(&pa, 0, sizeof pa);
+      const int N = p->n[m];
+      pa.g.N = N; pa.g.ni = inner > 1 ? 1 : 0; pa.g.I[0] = (int)inner; pa.g.Itot = inner;
+      pa.g.lines = outer * inner; pa.g.contig = inner == 1;
+      int TL = pa.g.contig ? std::max(1, std::min(64, 2048 / N)) : 16;
+      pa.g.TL = TL;
+      while (TL > 1 && pass_smem_bytes(pa.g, sizeof(double2)) > 96 * 1024) { TL /= 2; pa.g.TL = TL; }
+      ArrMap am;
+      memset(&am, 0, sizeof am);
+      am.os = (long long)N * inner; am.is[0] = 1; am.es = inner; am.vI[0] = am.vI[1] = am.vI[2] = 1 << 30; am.len = N;
+      pa.a_in0 = pa.a_in1 = pa.a_out0 = pa.a_out1 = am;
+      pa.in0 = F;
+      if (fa.cls_bits[m]) pa.out1 = F; else pa.out0 = F;
+      pa.fft = p->fft_sym[m];
+      if ((e = launch_pass<double2>(0, pa, st)) != cudaSuccess) bail(BTMV_E_CUDA, "FP64 symbol pass", e);
+    }
+    if (ret != BTMV_OK) break;
+    StoreArgs sa;
+    memset(&sa, 0, sizeof sa);
+    sa.store = store; sa.F = (const double2*)F; sa.d = d; sa.nsym = nsym; sa.prec = p->prec == BTMV_C128 ? 1 : 0;
+    for (int m = 0; m < d; ++m) { sa.n[m] = p->n[m]; sa.J[m] = sd.J[cls][m]; }
+    sa.s = p->s; sa.cls_off = sd.cls_off[cls]; sa.blk = sd.blk[cls];
+    if ((e = launch_store(sa, st)) != cudaSuccess) bail(BTMV_E_CUDA, "store kernel", e);
+  }
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess && ret == BTMV_OK) bail(BTMV_E_CUDA, "symbol build", e);
+  cudaFree(t_dev);
+  cudaFree(F);
+  if (ret != BTMV_OK) {
+    if (store != p->sym) cudaFree(store);
+    return ret;
+  }
+  p->sym = store;
+  p->sym_bytes = store_bytes;
+  sd.data = store;
+  p->symdev = sd;
+  p->nsym = nsym;
+  p->compressed = compressed;
+  p->has_sym = true;
+  return BTMV_OK;
+}
+
+// ------------------------------------------------------------ profiling
+static cudaEvent_t get_event(btmv_plan p) {
+  if (!p->pool.empty()) { cudaEvent_t e = p->pool.back(); p->pool.pop_back(); return e; }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+static void drain_profile(btmv_plan p) {
+  for (auto& r : p->pending) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) { p->acc_ms[r.kind] += ms; p->acc_n[r.kind] += 1; }
+    p->pool.push_back(r.a);
+    p->pool.push_back(r.b);
+  }
+  p->pending.clear();
+}
+
+struct ProfScope {
+  btmv_plan p;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  ProfScope(btmv_plan p_, int k, cudaStream_t s) : p(p_), kind(k), st(s) {
+    if (p->flags & BTMV_FLAG_PROFILE) { a = get_event(p); cudaEventRecord(a, st); }
+    p->launches++;
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = get_event(p);
+      cudaEventRecord(b, st);
+      p->pending.push_back({kind, a, b});
+      if (p->pending.size() > 65536) drain_profile(p);
+    }
+  }
+};
+
+// ------------------------------------------------------------ schedule
+static ArrMap contig_map(long long N, long long inner) {
+  ArrMap am;
+  memset(&am, 0, sizeof am);
+  am.os = N * inner; am.is[0] = 1; am.es = inner;
+  am.vI[0] = am.vI[1] = am.vI[2] = 1 << 30;
+  am.len = (int)N;
+  return am;
+}
+
+static void choose_tile(PassGeom& g, size_t esz) {
+  int TL = g.contig ? std::max(1, std::min(64, 2048 / g.N)) : 16;
+  g.TL = TL;
+  while (TL > 1 && pass_smem_bytes(g, esz) > 64 * 1024) { TL /= 2; g.TL = TL; }
+}
+
+template <class T>
+static btmv_status split_pass(btmv_plan p, int mode, int m, int nrhs, const void* in0, const void* in1,
+                              void* out0, void* out1, cudaStream_t st) {
+  long long outer = (long long)nrhs * p->c, inner = 1;
+  for (int q = 0; q < m; ++q) outer *= p->n[q];
+  for (int q = m + 1; q < p->d; ++q) inner *= p->n[q];
+  PassArgs pa;
+  memset(&pa, 0, sizeof pa);
+  const int N = p->n[m];
+  pa.g.N = N; pa.g.ni = inner > 1 ? 1 : 0; pa.g.I[0] = (int)inner; pa.g.Itot = inner;
+  pa.g.lines = outer * inner; pa.g.contig = inner == 1;
+  choose_tile(pa.g, sizeof(T));
+  pa.a_in0 = pa.a_in1 = pa.a_out0 = pa.a_out1 = contig_map(N, inner);
+  pa.in0 = in0; pa.in1 = in1; pa.out0 = out0; pa.out1 = out1;
+  pa.fft = p->fft_apply[m];
+  ProfScope ps(p, mode == 0 ? BTMV_K_FWD_SPLIT : BTMV_K_MERGE, st);
+  cudaError_t e = launch_pass<T>(mode, pa, st);
+  if (e != cudaSuccess) return fail(BTMV_E_CUDA, "split pass (dim %d, mode %d): %s", m, mode, cudaGetErrorString(e));
+  return BTMV_OK;
+}
+
+static void leaf_tiling(int N, int c, int nrhs, size_t esz, int& rq, int& Lt) {
+  rq = 1;
+  const size_t per = 3 * (size_t)c * (size_t)(N | 1) * esz;  // smem per (rhs, line)
+  Lt = (int)std::max<size_t>(1, (48 * 1024) / per);
+  if (Lt > 16) Lt = 16;
+  (void)nrhs;
+}
+
+template <class T>
+static btmv_status leaf_launch(btmv_plan p, int nrhs, int nn, const LeafNode* nodes, bool full,
+                               cudaStream_t st) {
+  LeafArgs la;
+  memset(&la, 0, sizeof la);
+  const int d = p->d;
+  la.N = full ? 2 * p->n[d - 1] : p->n[d - 1];
+  la.c = p->c;
+  la.nrhs = nrhs;
+  la.dl = d - 1;
+  la.lines = 1;
+  for (int m = 0; m < d - 1; ++m) { la.ext[m] = full ? 2 * p->n[m] : p->n[m]; la.lines *= la.ext[m]; }
+  la.comp_stride = full ? p->s2 : p->s;
+  la.rhs_stride = la.comp_stride * p->c;
+  la.split = full ? 0 : 1;
+  leaf_tiling(la.N, la.c, nrhs, sizeof(T), la.rq, la.Lt);
+  const long long nlt = (la.lines + la.Lt - 1) / la.Lt;
+  const long long nrc = (nrhs + la.rq - 1) / la.rq;
+  la.tiles_per_node = nlt * nrc;
+  la.nnodes = nn;
+  for (int i = 0; i < nn; ++i) la.nodes[i] = nodes[i];
+  la.fft = p->fft_apply[d - 1];
+  la.sym = p->symdev;
+  ProfScope ps(p, full ? BTMV_K_FULL_LEAF : BTMV_K_LEAF, st);
+  cudaError_t e = launch_leaf<T>(la, st);
+  if (e != cudaSuccess) return fail(BTMV_E_CUDA, "leaf pass: %s", cudaGetErrorString(e));
+  return BTMV_OK;
+}
+
+#define TRY(x) do { btmv_status s_ = (x); if (s_ != BTMV_OK) return s_; } while (0)
+
+// Depth-first traversal of Algorithm 1 (see btmv_apply in btmv.h).
+template <class T>
+static btmv_status split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, int nrhs, cudaStream_t st);
+
+template <class T>
+static btmv_status split_descend(btmv_plan p, int m, void* buf, int prefix, int nrhs, cudaStream_t st) {
+  void* Wm = p->W[m];
+  TRY(split_pass<T>(p, 0, m, nrhs, buf, nullptr, buf, Wm, st));
+  TRY(split_children<T>(p, m, buf, Wm, prefix, prefix | (1 << m), nrhs, st));
+  TRY(split_pass<T>(p, 1, m, nrhs, buf, Wm, buf, nullptr, st));
+  return BTMV_OK;
+}
+
+template <class T>
+static btmv_status split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, int nrhs, cudaStream_t st) {
+  if (m + 1 == p->d - 1) {
+    LeafNode nodes[2] = {{e, e, pe}, {o, o, po}};
+    return leaf_launch<T>(p, nrhs, 2, nodes, false, st);
+  }
+  TRY(split_descend<T>(p, m + 1, e, pe, nrhs, st));
+  TRY(split_descend<T>(p, m + 1, o, po, nrhs, st));
+  return BTMV_OK;
+}
+
+template <class T>
+static btmv_status split_apply(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
+  if (p->d == 1) {
+    LeafNode nd = {x, y, 0};
+    return leaf_launch<T>(p, nrhs, 1, &nd, false, st);
+  }
+  TRY(split_pass<T>(p, 0, 0, nrhs, x, nullptr, y, p->W[0], st));
+  TRY(split_children<T>(p, 0, y, p->W[0], 0, 1, nrhs, st));
+  TRY(split_pass<T>(p, 1, 0, nrhs, y, p->W[0], y, nullptr, st));
+  return BTMV_OK;
+}
+
+// Plain full embedding with own kernels: pad fused into the first forward
+// pass, multiply into the last-dim pass, projection into the last inverse pass.
+template <class T>
+static btmv_status full_apply(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
+  const int d = p->d;
+  void* Z = p->W[0];
+  const size_t esz = sizeof(T);
+  if (d == 1) {
+    const size_t rows = (size_t)nrhs * p->c;
+    const size_t nb = (size_t)p->n[0] * esz;
+    {
+      ProfScope ps(p, BTMV_K_FULL_FWD, st);
+      CUDA_TRY(cudaMemsetAsync(Z, 0, rows * 2 * nb, st));
+      CUDA_TRY(cudaMemcpy2DAsync(Z, 2 * nb, x, nb, nb, rows, cudaMemcpyDeviceToDevice, st));
+    }
+    LeafNode nd = {Z, Z, 0};
+    TRY(leaf_launch<T>(p, nrhs, 1, &nd, true, st));
+    ProfScope ps(p, BTMV_K_FULL_INV, st);
+    CUDA_TRY(cudaMemcpy2DAsync(y, nb, Z, 2 * nb, nb, rows, cudaMemcpyDeviceToDevice, st));
+    return BTMV_OK;
+  }
+  // strides of x/y (n grid) and Z (2n grid)
+  long long sx[MAX_D], sz[MAX_D];
+  sx[d - 1] = 1; sz[d - 1] = 1;
+  for (int m = d - 2; m >= 0; --m) { sx[m] = sx[m + 1] * p->n[m + 1]; sz[m] = sz[m + 1] * 2 * p->n[m + 1]; }
+  // first pass: dim 0, x (n grid, zero padded) -> Z (2n grid), every Z line written
+  {
+    PassArgs pa;
+    memset(&pa, 0, sizeof pa);
+    pa.g.N = 2 * p->n[0];
+    pa.g.ni = d - 1;
+    pa.g.Itot = 1;
+    for (int j = 0; j < d - 1; ++j) { pa.g.I[j] = 2 * p->n[j + 1]; pa.g.Itot *= pa.g.I[j]; }
+    pa.g.lines = (long long)nrhs * p->c * pa.g.Itot;
+    pa.g.contig = 0;
+    choose_tile(pa.g, esz);
+    ArrMap ai, ao;
+    memset(&ai, 0, sizeof ai);
+    memset(&ao, 0, sizeof ao);
+    ai.os = p->s; ai.es = sx[0]; ai.len = p->n[0];
+    ao.os = p->s2; ao.es = sz[0]; ao.len = 2 * p->n[0];
+    for (int j = 0; j < 3; ++j) { ai.vI[j] = 1 << 30; ao.vI[j] = 1 << 30; }
+    for (int j = 0; j < d - 1; ++j) { ai.is[j] = sx[j + 1]; ai.vI[j] = p->n[j + 1]; ao.is[j] = sz[j + 1]; }
+    pa.a_in0 = pa.a_in1 = ai;
+    pa.a_out0 = pa.a_out1 = ao;
+    pa.in0 = x; pa.out0 = Z;
+    pa.fft = p->fft_apply[0];
+    ProfScope ps(p, BTMV_K_FULL_FWD, st);
+    cudaError_t e = launch_pass<T>(0, pa, st);
+    if (e != cudaSuccess) return fail(BTMV_E_CUDA, "full first pass: %s", cudaGetErrorString(e));
+  }
+  auto big_pass = [&](int mode, int m) -> btmv_status {
+    long long outer = (long long)nrhs * p->c, inner = 1;
+    for (int q = 0; q < m; ++q) outer *= 2 * p->n[q];
+    for (int q = m + 1; q < d; ++q) inner *= 2 * p->n[q];
+    PassArgs pa;
+    memset(&pa, 0, sizeof pa);
+    const int N = 2 * p->n[m];
+    pa.g.N = N; pa.g.ni = inner > 1 ? 1 : 0; pa.g.I[0] = (int)inner; pa.g.Itot = inner;
+    pa.g.lines = outer * inner; pa.g.contig = inner == 1;
+    choose_tile(pa.g, esz);
+    pa.a_in0 = pa.a_in1 = pa.a_out0 = pa.a_out1 = contig_map(N, inner);
+    pa.in0 = Z; pa.out0 = Z;
+    pa.fft = p->fft_apply[m];
+    ProfScope ps(p, mode == 0 ? BTMV_K_FULL_FWD : BTMV_K_FULL_INV, st);
+    cudaError_t e = launch_pass<T>(mode, pa, st);
+    if (e != cudaSuccess) return fail(BTMV_E_CUDA, "full pass dim %d: %s", m, cudaGetErrorString(e));
+    return BTMV_OK;
+  };
+  for (int m = 1; m < d - 1; ++m) TRY(big_pass(0, m));
+  {
+    LeafNode nd = {Z, Z, 0};
+    TRY(leaf_launch<T>(p, nrhs, 1, &nd, true, st));
+  }
+  for (int m = d - 2; m >= 1; --m) TRY(big_pass(1, m));
+  // last pass: dim 0 inverse on the surviving lines, projected into y
+  {
+    PassArgs pa;
+    memset(&pa, 0, sizeof pa);
+    pa.g.N = 2 * p->n[0];
+    pa.g.ni = d - 1;
+    pa.g.Itot = 1;
+    for (int j = 0; j < d - 1; ++j) { pa.g.I[j] = p->n[j + 1]; pa.g.Itot *= pa.g.I[j]; }
+    pa.g.lines = (long long)nrhs * p->c * pa.g.Itot;
+    pa.g.contig = 0;
+    choose_tile(pa.g, esz);
+    ArrMap ai, ao;
+    memset(&ai, 0, sizeof ai);
+    memset(&ao, 0, sizeof ao);
+    ai.os = p->s2; ai.es = sz[0]; ai.len = 2 * p->n[0];
+    ao.os = p->s; ao.es = sx[0]; ao.len = p->n[0];
+    for (int j = 0; j < 3; ++j) { ai.vI[j] = 1 << 30; ao.vI[j] = 1 << 30; }
+    for (int j = 0; j < d - 1; ++j) { ai.is[j] = sz[j + 1]; ao.is[j] = sx[j + 1]; }
+    pa.a_in0 = pa.a_in1 = ai;
+    pa.a_out0 = pa.a_out1 = ao;
+    pa.in0 = Z; pa.out0 = y;
+    pa.fft = p->fft_apply[0];
+    ProfScope ps(p, BTMV_K_FULL_INV, st);
+    cudaError_t e = launch_pass<T>(1, pa, st);
+    if (e != cudaSuccess) return fail(BTMV_E_CUDA, "full last pass: %s", cudaGetErrorString(e));
+  }
+  return BTMV_OK;
+}
+
+static int is_device_ptr(const void* ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) { cudaGetLastError(); return 0; }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static btmv_status apply_device(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
+  if (p->algo == BTMV_ALGO_SPLIT)
+    return p->prec == BTMV_C64 ? split_apply<float2>(p, x, y, nrhs, st) : split_apply<double2>(p, x, y, nrhs, st);
+  return p->prec == BTMV_C64 ? full_apply<float2>(p, x, y, nrhs, st) : full_apply<double2>(p, x, y, nrhs, st);
+}
+
+static btmv_status check_apply(btmv_plan p, const void* x, void* y, int nrhs) {
+  if (!p) return fail(BTMV_E_ARG, "apply: plan is NULL");
+  if (nrhs < 0 || nrhs > p->max_rhs) return fail(BTMV_E_ARG, "apply: nrhs=%d outside [0,%d]", nrhs, p->max_rhs);
+  if (!p->has_sym) return fail(BTMV_E_STATE, "apply: btmv_set_kernel has not been called");
+  if (nrhs == 0) return BTMV_OK;
+  if (!x || !y) return fail(BTMV_E_ARG, "apply: x or y is NULL");
+  if (((uintptr_t)x | (uintptr_t)y) & 15) return fail(BTMV_E_ARG, "apply: x and y must be 16-byte aligned");
+  const size_t V = (size_t)nrhs * p->c * p->s * p->esz;
+  const char* xa = (const char*)x;
+  const char* ya = (const char*)y;
+  if (xa < ya + V && ya < xa + V) return fail(BTMV_E_ARG, "apply: x and y overlap");
+  return BTMV_OK;
+}
+
+extern "C" btmv_status btmv_apply(btmv_plan p, const void* x, void* y, int nrhs, void* stream) {
+  g_err.clear();
+  TRY(check_apply(p, x, y, nrhs));
+  if (nrhs == 0) return BTMV_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int dx = is_device_ptr(x), dy = is_device_ptr(y);
+  p->launches = 0;
+  if (dx && dy) return apply_device(p, x, y, nrhs, st);
+  // host staging
+  const size_t V = (size_t)nrhs * p->c * p->s * p->esz;
+  const size_t Vmax = (size_t)p->max_rhs * p->c * p->s * p->esz;
+  if (!dx && !p->stage_x) CUDA_TRY(cudaMalloc(&p->stage_x, Vmax));
+  if (!dy && !p->stage_y) CUDA_TRY(cudaMalloc(&p->stage_y, Vmax));
+  const void* xd = x;
+  void* yd = y;
+  if (!dx) {
+    ProfScope ps(p, BTMV_K_COPY, st);
+    CUDA_TRY(cudaMemcpyAsync(p->stage_x, x, V, cudaMemcpyHostToDevice, st));
+    xd = p->stage_x;
+  }
+  if (!dy) yd = p->stage_y;
+  TRY(apply_device(p, xd, yd, nrhs, st));
+  if (!dy) {
+    ProfScope ps(p, BTMV_K_COPY, st);
+    CUDA_TRY(cudaMemcpyAsync(y, yd, V, cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return BTMV_OK;
+}
+
+extern "C" btmv_status btmv_apply_batched(int count, const btmv_plan* plans, const void* const* x, void* const* y,
+                                          const int* nrhs, void* stream) {
+  g_err.clear();
+  if (count < 0) return fail(BTMV_E_ARG, "apply_batched: count < 0");
+  if (count == 0) return BTMV_OK;
+  if (!plans || !x || !y || !nrhs) return fail(BTMV_E_ARG, "apply_batched: NULL array");
+  for (int i = 0; i < count; ++i) {
+    TRY(check_apply(plans[i], x[i], y[i], nrhs[i]));
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return fail(BTMV_E_ARG, "apply_batched: plan %d repeated at %d", j, i);
+    if (nrhs[i] && (!is_device_ptr(x[i]) || !is_device_ptr(y[i])))
+      return fail(BTMV_E_ARG, "apply_batched: entry %d is not a device pointer", i);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < count; ++i) {
+    if (!nrhs[i]) continue;
+    plans[i]->launches = 0;
+    TRY(apply_device(plans[i], x[i], y[i], nrhs[i], st));
+  }
+  return BTMV_OK;
+}
+
+extern "C" btmv_status btmv_destroy(btmv_plan p) {
+  g_err.clear();
+  if (!p) return BTMV_OK;
+  cudaDeviceSynchronize();
+  free_plan(p);
+  return BTMV_OK;
+}
+
+extern "C" const char* btmv_last_error(void) { return g_err.c_str(); }
+
+static int launches_per_apply(btmv_plan p) {
+  const int d = p->d;
+  if (p->algo == BTMV_ALGO_SPLIT) {
+    if (d == 1) return 1;
+    // forward + merge per internal node of levels 0..d-2, one leaf launch per level-(d-2) node
+    int n = 0;
+    for (int m = 0; m < d - 1; ++m) n += 2 * (1 << m);
+    n += 1 << (d - 2);
+    return n;
+  }
+  if (d == 1) return 3;
+  return 2 * (d - 2) + 3;
+}
+
+extern "C" btmv_status btmv_plan_get_info(btmv_plan p, btmv_plan_info_t* info) {
+  g_err.clear();
+  if (!p || !info) return fail(BTMV_E_ARG, "plan_get_info: NULL argument");
+  memset(info, 0, sizeof *info);
+  info->d = p->d; info->c = p->c; info->precision = p->prec; info->algo = p->algo; info->max_rhs = p->max_rhs;
+  for (int m = 0; m < MAX_D; ++m) info->n[m] = m < p->d ? p->n[m] : 0;
+  info->nsym = p->nsym;
+  info->compressed = p->compressed;
+  info->has_symbol = p->has_sym ? 1 : 0;
+  info->launches_per_apply = launches_per_apply(p);
+  info->symbol_bytes = p->sym_bytes;
+  info->workspace_bytes = p->ws_bytes;
+  info->table_bytes = p->tab.bytes;
+  info->vector_bytes = (size_t)p->c * p->s * p->esz;
+  return BTMV_OK;
+}
+
+extern "C" btmv_status btmv_get_symbol(btmv_plan p, void* out, size_t bytes) {
+  g_err.clear();
+  if (!p || !out) return fail(BTMV_E_ARG, "get_symbol: NULL argument");
+  if (!p->has_sym) return fail(BTMV_E_STATE, "get_symbol: no symbol");
+  if (bytes < p->sym_bytes) return fail(BTMV_E_ARG, "get_symbol: need %zu bytes", p->sym_bytes);
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(out, p->sym, p->sym_bytes, cudaMemcpyDeviceToHost));
+  return BTMV_OK;
+}
+
+extern "C" btmv_status btmv_profile_read(btmv_plan p, double* ms_total, int64_t* launches) {
+  g_err.clear();
+  if (!p || !ms_total || !launches) return fail(BTMV_E_ARG, "profile_read: NULL argument");
+  if (!(p->flags & BTMV_FLAG_PROFILE)) return fail(BTMV_E_STATE, "profile_read: plan created without BTMV_FLAG_PROFILE");
+  drain_profile(p);
+  for (int k = 0; k < BTMV_K_NKINDS; ++k) {
+    ms_total[k] = p->acc_ms[k];
+    launches[k] = p->acc_n[k];
+    p->acc_ms[k] = 0;
+    p->acc_n[k] = 0;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(BTMV_E_CUDA, "profile_read: %s", cudaGetErrorString(e));
+  return BTMV_OK;
+}

@@ -1,0 +1,409 @@
+// Line-pass kernels of the split-FFT block Toeplitz product.
+//
+//   k_pass<T, 0>  forward split pass along one level (Sec. II.A splitting
+//                 property): one read of the parent node, both children
+//                 written -- even = FFT_n(v), odd = FFT_n(P v).
+//   k_pass<T, 1>  backward merge pass (Sec. II.A merge, Algorithm 1 mrgBrn
+//                 + iFFT): out = IFFT_n(v_even) + conj(P) IFFT_n(v_odd).
+//   k_leaf<T>     leaf pass along the last level: both halves, the c x c
+//                 symbol multiply (Algorithm 1 mulBrn with T[bId]) and the
+//                 merge, fused per contiguous line.
+//   k_fold / k_store  FP64 symbol build (see btmv_set_kernel).
+//
+// Every pass stages a tile of lines through shared memory: coalesced global
+// loads, Stockham stages ping-ponging between smem buffers, coalesced stores.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace btmv {
+
+static __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static __host__ __device__ inline size_t pass_hdr_bytes(int TL) {
+  return align_up((size_t)TL * (4 * sizeof(long long) + sizeof(int)), 16);
+}
+
+size_t pass_smem_bytes(const PassGeom& g, size_t esz) {
+  const size_t ls = g.contig ? (size_t)(g.N | 1) : 1;
+  const size_t buf = g.contig ? (size_t)g.TL * ls : (size_t)g.TL * g.N;
+  return pass_hdr_bytes(g.TL) + 3 * buf * esz;
+}
+
+static __host__ __device__ inline size_t leaf_hdr_bytes(int Lt) {
+  return align_up((size_t)Lt * 4 * sizeof(int), 16);
+}
+
+size_t leaf_smem_bytes(int N, int c, int rq, int Lt, size_t esz) {
+  const size_t ls = (size_t)(N | 1);
+  return leaf_hdr_bytes(Lt) + 3 * (size_t)rq * c * Lt * ls * esz;
+}
+
+template <class T> __device__ __forceinline__ T czero() { T z; z.x = 0; z.y = 0; return z; }
+
+// ----------------------------------------------------------------- k_pass
+template <class T>
+__device__ __forceinline__ void pass_load(T* __restrict__ d0, T* __restrict__ d1, const T* __restrict__ src,
+                                          const ArrMap& m, const long long* __restrict__ off,
+                                          const int* __restrict__ okl, const PassGeom& g, int ls, int es,
+                                          const T* __restrict__ ph, bool tw0) {
+  // d0 receives the line (times P when tw0), d1 (if non-null) receives P * line
+  const int TL = g.TL, N = g.N;
+  const int total = TL * N;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    int line, k;
+    if (g.contig) { line = e / N; k = e - line * N; }
+    else          { line = e % TL; k = e / TL; }
+    T v = czero<T>();
+    if ((okl[line] & 2) && k < m.len) v = src[off[line] + (long long)k * m.es];
+    const int si = line * ls + k * es;
+    if (d1) {
+      d0[si] = v;
+      d1[si] = cmul(v, __ldg(&ph[k]));
+    } else {
+      d0[si] = tw0 ? cmul(v, __ldg(&ph[k])) : v;
+    }
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void pass_store(T* __restrict__ dst, const T* __restrict__ r0,
+                                           const T* __restrict__ r1, const ArrMap& m,
+                                           const long long* __restrict__ off, const int* __restrict__ okl,
+                                           const PassGeom& g, int ls, int es, const T* __restrict__ ph) {
+  const int TL = g.TL, N = g.N;
+  const int total = TL * N;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    int line, k;
+    if (g.contig) { line = e / N; k = e - line * N; }
+    else          { line = e % TL; k = e / TL; }
+    if (!(okl[line] & 1) || k >= m.len) continue;
+    const int si = line * ls + k * es;
+    T v = r0[si];
+    if (r1) v = cadd(v, cmulc(r1[si], __ldg(&ph[k])));
+    dst[off[line] + (long long)k * m.es] = v;
+  }
+}
+
+template <class T, int MODE, bool LF>
+__device__ __forceinline__ void pass_body(const PassArgs& a, unsigned char* smem) {
+  const PassGeom& g = a.g;
+  const int TL = g.TL, N = g.N;
+  const int ls = g.contig ? (N | 1) : 1;
+  const int es = g.contig ? 1 : TL;
+  const int bufsz = g.contig ? TL * ls : TL * N;
+  long long* offs = (long long*)smem;         // [4][TL]
+  int* okl = (int*)(offs + 4 * TL);           // [TL]
+  T* B0 = (T*)(smem + pass_hdr_bytes(TL));
+  T* B1 = B0 + bufsz;
+  T* B2 = B1 + bufsz;
+  const T* ph = (const T*)a.fft.ph;
+
+  const long long tile0 = (long long)blockIdx.x * TL;
+  for (int l = threadIdx.x; l < TL; l += blockDim.x) {
+    const long long gl = tile0 + l;
+    int ok = gl < g.lines;
+    long long o = 0;
+    int ii[3] = {0, 0, 0};
+    if (ok) {
+      o = gl / g.Itot;
+      long long r = gl - o * g.Itot;
+      for (int j = g.ni - 1; j >= 0; --j) { ii[j] = (int)(r % g.I[j]); r /= g.I[j]; }
+    }
+    const ArrMap* ms[4] = {&a.a_in0, &a.a_in1, &a.a_out0, &a.a_out1};
+    for (int q = 0; q < 4; ++q) {
+      long long v = o * ms[q]->os;
+      for (int j = 0; j < g.ni; ++j) v += (long long)ii[j] * ms[q]->is[j];
+      offs[q * TL + l] = v;
+    }
+    int valid = ok;
+    for (int j = 0; j < g.ni; ++j)
+      if (ii[j] >= a.a_in0.vI[j]) valid = 0;
+    okl[l] = ok | (valid << 1);
+  }
+  __syncthreads();
+
+  if (MODE == 0) {
+    const bool both = a.out0 && a.out1;
+    if (both) {
+      pass_load<T>(B0, B1, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es, ph, false);
+      __syncthreads();
+      T* r0 = fft_lines<false, LF>(B0, B2, TL, ls, es, a.fft);
+      pass_store<T>((T*)a.out0, r0, nullptr, a.a_out0, offs + 2 * TL, okl, g, ls, es, ph);
+      __syncthreads();
+      T* r1 = fft_lines<false, LF>(B1, (r0 == B0) ? B2 : B0, TL, ls, es, a.fft);
+      pass_store<T>((T*)a.out1, r1, nullptr, a.a_out1, offs + 3 * TL, okl, g, ls, es, ph);
+    } else {
+      const bool odd = a.out1 != nullptr;
+      pass_load<T>(B0, nullptr, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es, ph, odd);
+      __syncthreads();
+      T* r = fft_lines<false, LF>(B0, B1, TL, ls, es, a.fft);
+      if (odd) pass_store<T>((T*)a.out1, r, nullptr, a.a_out1, offs + 3 * TL, okl, g, ls, es, ph);
+      else     pass_store<T>((T*)a.out0, r, nullptr, a.a_out0, offs + 2 * TL, okl, g, ls, es, ph);
+    }
+  } else {
+    const bool two = a.in1 != nullptr;
+    pass_load<T>(B0, nullptr, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es, ph, false);
+    if (two) pass_load<T>(B1, nullptr, (const T*)a.in1, a.a_in1, offs + TL, okl, g, ls, es, ph, false);
+    __syncthreads();
+    T* r0 = fft_lines<true, LF>(B0, B2, TL, ls, es, a.fft);
+    T* r1 = nullptr;
+    if (two) r1 = fft_lines<true, LF>(B1, (r0 == B0) ? B2 : B0, TL, ls, es, a.fft);
+    pass_store<T>((T*)a.out0, r0, r1, a.a_out0, offs + 2 * TL, okl, g, ls, es, ph);
+  }
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (a.g.contig) pass_body<T, MODE, false>(a, smem);
+  else            pass_body<T, MODE, true>(a, smem);
+}
+
+static const size_t kMaxSmem = 227 * 1024;
+
+template <class T>
+cudaError_t launch_pass(int mode, const PassArgs& a, cudaStream_t st) {
+  const size_t sm = pass_smem_bytes(a.g, sizeof(T));
+  if (sm > kMaxSmem) return cudaErrorInvalidValue;
+  const long long nt = (a.g.lines + a.g.TL - 1) / a.g.TL;
+  if (nt <= 0) return cudaSuccess;
+  if (nt > 0x7fffffffLL) return cudaErrorInvalidValue;
+  static bool attr0 = false, attr1 = false;
+  if (mode == 0) {
+    if (!attr0) { cudaFuncSetAttribute(k_pass<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem); attr0 = true; }
+    k_pass<T, 0><<<(unsigned)nt, 256, sm, st>>>(a);
+  } else {
+    if (!attr1) { cudaFuncSetAttribute(k_pass<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem); attr1 = true; }
+    k_pass<T, 1><<<(unsigned)nt, 256, sm, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- k_leaf
+// Stored-symbol lookup: f = full-grid frequency per dim (f_m in [0, 2 n_m)).
+__device__ __forceinline__ long long sym_index(const SymDev& S, const int* f, int& fold, int& cls) {
+  cls = 0;
+  fold = 0;
+  for (int m = 0; m < S.d; ++m) cls = (cls << 1) | (f[m] & 1);
+  long long lin = 0;
+  for (int m = 0; m < S.d; ++m) {
+    int fm = f[m];
+    if (S.compressed && fm > S.n[m]) { fm = 2 * S.n[m] - fm; fold |= 1 << m; }
+    lin = lin * S.J[cls][m] + (fm >> 1);
+  }
+  return S.cls_off[cls] + lin;
+}
+
+template <class T>
+__device__ __forceinline__ void leaf_multiply(T* __restrict__ R, const LeafArgs& a, int b,
+                                              const int* __restrict__ fpre, int ls) {
+  const int N = a.N, Lt = a.Lt, c = a.c;
+  const int total = a.rq * Lt * N;
+  const T* __restrict__ S = (const T*)a.sym.data;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int l = e % N;
+    const int rest = e / N;
+    const int li = rest % Lt;
+    const int q = rest / Lt;
+    if (fpre[li * 4 + 3] == 0) continue;   // line beyond the node
+    int f[MAX_D];
+    for (int m = 0; m < a.dl; ++m) f[m] = fpre[li * 4 + m];
+    f[a.dl] = a.split ? 2 * l + b : l;
+    int fold, cls;
+    const long long base = sym_index(a.sym, f, fold, cls);
+    const long long blk = a.sym.blk[cls];
+    T x[3], y[3];
+    for (int ai = 0; ai < c; ++ai) x[ai] = R[((q * c + ai) * Lt + li) * ls + l];
+    for (int ai = 0; ai < c; ++ai) {
+      T acc = czero<T>();
+      for (int bi = 0; bi < c; ++bi) {
+        const int kk = a.sym.comp[ai][bi];
+        T s = __ldg(&S[base + kk * blk]);
+        if (__popc(a.sym.oddmask[kk] & fold) & 1) { s.x = -s.x; s.y = -s.y; }
+        acc = cadd(acc, cmul(s, x[bi]));
+      }
+      y[ai] = acc;
+    }
+    for (int ai = 0; ai < c; ++ai) R[((q * c + ai) * Lt + li) * ls + l] = y[ai];
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_leaf(const LeafArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = a.N, c = a.c, rq = a.rq, Lt = a.Lt;
+  const int NV = rq * c * Lt;
+  const int ls = N | 1;
+  const int bufsz = NV * ls;
+  int* fpre = (int*)smem;                    // [Lt][4]: f of line dims, valid flag
+  T* X = (T*)(smem + leaf_hdr_bytes(Lt));
+  T* B0 = X + bufsz;
+  T* B1 = B0 + bufsz;
+  const T* ph = (const T*)a.fft.ph;
+
+  const LeafNode nd = a.nodes[blockIdx.y];
+  const long long nlt = (a.lines + Lt - 1) / Lt;
+  const long long tile = blockIdx.x;
+  const long long lt = tile % nlt;
+  const int q0 = (int)(tile / nlt) * rq;
+  const long long l0 = lt * Lt;
+
+  for (int li = threadIdx.x; li < Lt; li += blockDim.x) {
+    const long long gl = l0 + li;
+    int ok = gl < a.lines;
+    long long r = ok ? gl : 0;
+    for (int m = a.dl - 1; m >= 0; --m) {
+      const int im = (int)(r % a.ext[m]);
+      r /= a.ext[m];
+      fpre[li * 4 + m] = a.split ? 2 * im + ((nd.prefix >> m) & 1) : im;
+    }
+    fpre[li * 4 + 3] = ok;
+  }
+  __syncthreads();
+
+  const T* __restrict__ in = (const T*)nd.in;
+  const int totalv = NV * N;
+  for (int e = threadIdx.x; e < totalv; e += blockDim.x) {
+    const int vl = e / N;
+    const int k = e - vl * N;
+    const int li = vl % Lt;
+    const int qa = vl / Lt;
+    const int ai = qa % c;
+    const int q = q0 + qa / c;
+    T v = czero<T>();
+    if (fpre[li * 4 + 3] && q < a.nrhs)
+      v = in[(long long)q * a.rhs_stride + (long long)ai * a.comp_stride + (l0 + li) * N + k];
+    B0[vl * ls + k] = v;
+    if (a.split) X[vl * ls + k] = cmul(v, __ldg(&ph[k]));
+  }
+  __syncthreads();
+
+  // even half (or the whole 2n line for the plain embedding)
+  T* r = fft_lines<false, false>(B0, B1, NV, ls, 1, a.fft);
+  leaf_multiply<T>(r, a, 0, fpre, ls);
+  __syncthreads();
+  T* A0 = fft_lines<true, false>(r, (r == B0) ? B1 : B0, NV, ls, 1, a.fft);
+  T* A1 = nullptr;
+  if (a.split) {
+    // odd half: twiddled input in X, scratch = the buffer not holding A0
+    T* S = (A0 == B0) ? B1 : B0;
+    T* r1 = fft_lines<false, false>(X, S, NV, ls, 1, a.fft);
+    leaf_multiply<T>(r1, a, 1, fpre, ls);
+    __syncthreads();
+    A1 = fft_lines<true, false>(r1, (r1 == X) ? S : X, NV, ls, 1, a.fft);
+  }
+
+  T* __restrict__ out = (T*)nd.out;
+  for (int e = threadIdx.x; e < totalv; e += blockDim.x) {
+    const int vl = e / N;
+    const int k = e - vl * N;
+    const int li = vl % Lt;
+    const int qa = vl / Lt;
+    const int ai = qa % c;
+    const int q = q0 + qa / c;
+    if (!fpre[li * 4 + 3] || q >= a.nrhs) continue;
+    T v = A0[vl * ls + k];
+    if (A1) v = cadd(v, cmulc(A1[vl * ls + k], __ldg(&ph[k])));
+    out[(long long)q * a.rhs_stride + (long long)ai * a.comp_stride + (l0 + li) * N + k] = v;
+  }
+}
+
+template <class T>
+cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t st) {
+  const size_t sm = leaf_smem_bytes(a.N, a.c, a.rq, a.Lt, sizeof(T));
+  if (sm > kMaxSmem) return cudaErrorInvalidValue;
+  if (a.tiles_per_node <= 0 || a.nnodes <= 0) return cudaSuccess;
+  if (a.tiles_per_node > 0x7fffffffLL || a.nnodes > MAX_LEAF_NODES) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) { cudaFuncSetAttribute(k_leaf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem); attr = true; }
+  dim3 grid((unsigned)a.tiles_per_node, (unsigned)a.nnodes);
+  k_leaf<T><<<grid, 256, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- symbol
+// F[kk][k] = scale * sum_{h in {0,1}^d} (-1)^{<h, b>} c~_kk[k + h n]  with
+// c~[k + n] = t[k - n] for k > 0 and the free entry s0 = 0 for k = 0: the
+// 2n-point embedded generator folded onto n points for parity class b, so
+// that DFT_n(P_b F) is the leaf part S_b.
+__global__ void k_fold(const FoldArgs a) {
+  const long long total = (long long)a.nsym * a.s;
+  long long tb = 1;
+  if (!a.parity_layout)
+    for (int m = 0; m < a.d; ++m) tb *= (2 * a.n[m] - 1);
+  else
+    tb = a.s;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int kk = (int)(idx / a.s);
+    long long r = idx - (long long)kk * a.s;
+    int k[MAX_D];
+    for (int m = a.d - 1; m >= 0; --m) { k[m] = (int)(r % a.n[m]); r /= a.n[m]; }
+    const int A = a.pairs[kk][0], B = a.pairs[kk][1];
+    const double2* tb0 = a.t + (long long)(A * a.c + B) * tb;
+    double ax = 0.0, ay = 0.0;
+    for (int h = 0; h < (1 << a.d); ++h) {
+      double sg = 1.0;
+      bool ok = true;
+      long long toff = 0;
+      for (int m = 0; m < a.d; ++m) {
+        int p;
+        if ((h >> m) & 1) {
+          if (k[m] == 0) { ok = false; break; }
+          p = k[m] - a.n[m];
+          if (a.cls_bits[m]) sg = -sg;
+        } else {
+          p = k[m];
+        }
+        if (a.parity_layout) {
+          if (p < 0) { sg *= (double)a.par[A][B][m]; p = -p; }
+          toff = toff * a.n[m] + p;
+        } else {
+          toff = toff * (2 * a.n[m] - 1) + (p + a.n[m] - 1);
+        }
+      }
+      if (!ok) continue;
+      const double2 v = tb0[toff];
+      ax += sg * v.x;
+      ay += sg * v.y;
+    }
+    a.F[idx] = make_double2(ax * a.scale, ay * a.scale);
+  }
+}
+
+__global__ void k_store(const StoreArgs a) {
+  const long long total = (long long)a.nsym * a.blk;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int kk = (int)(idx / a.blk);
+    long long r = idx - (long long)kk * a.blk;
+    long long lin = 0, mul = 1;
+    for (int m = a.d - 1; m >= 0; --m) {
+      const int j = (int)(r % a.J[m]);
+      r /= a.J[m];
+      lin += (long long)j * mul;
+      mul *= a.n[m];
+    }
+    const double2 v = a.F[(long long)kk * a.s + lin];
+    if (a.prec == 0) ((float2*)a.store)[a.cls_off + idx] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+    else             ((double2*)a.store)[a.cls_off + idx] = v;
+  }
+}
+
+cudaError_t launch_fold(const FoldArgs& a, cudaStream_t st) {
+  k_fold<<<152 * 8, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_store(const StoreArgs& a, cudaStream_t st) {
+  k_store<<<152 * 8, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_pass<float2>(int, const PassArgs&, cudaStream_t);
+template cudaError_t launch_pass<double2>(int, const PassArgs&, cudaStream_t);
+template cudaError_t launch_leaf<float2>(const LeafArgs&, cudaStream_t);
+template cudaError_t launch_leaf<double2>(const LeafArgs&, cudaStream_t);
+
+}  // namespace btmv

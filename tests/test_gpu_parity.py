@@ -1,0 +1,170 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Gates: relative L2 error <= 1e-5 for complex64 and <= 1e-12 for complex128
+(the FP64 GPU mode), element by element over the whole output.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import embed as OE
+from oracle import toeplitz as OT
+from tests.gpu_util import TOL, rel, round_input, run_btmv
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+bt = pytest.importorskip("paper_2406_17981_gb300.btmv")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    bt.lib()
+
+
+SIZES = [(1,), (2,), (5,), (16,), (60,), (128,), (3, 4), (7, 6), (12, 10), (1, 8), (4, 1),
+         (16, 16), (5, 6, 7), (8, 8, 8), (3, 1, 4), (24, 12, 10), (2, 3, 4, 5), (20, 21, 14)]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("c", [1, 3])
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("algo", [0, 1])
+def test_random_generator_vs_oracle(n, c, precision, algo):
+    t = W.random_generator(n, c, seed=100 + len(n))
+    x = W.random_vector(n, c, seed=200 + sum(n), nrhs=2)
+    y = run_btmv(t, x, n, c, precision, algo)
+    ref = OE.embed_matvec(t, round_input(x, precision))
+    assert rel(y, ref) <= TOL[precision]
+
+
+def test_config_d2_64_c1_c128_vs_direct_sum():
+    """64 x 64, scalar, random complex generator, complex128 vs the direct sum."""
+    cfg = W.WORKLOADS["d2_64_c1_random_c128"]
+    n = cfg["n"]
+    t = W.random_generator(n, 1, seed=cfg["t_seed"])
+    x = W.random_vector(n, 1, seed=cfg["x_seed"])
+    for algo in (0, 1):
+        y = run_btmv(t, x, n, 1, 1, algo)
+        ref = OT.direct_matvec(t, x)
+        assert rel(y, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [(6, 5, 7), (16, 12, 20), (32, 32, 32)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_green_parity_compressed_symbol(n, precision):
+    t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    x = W.random_vector(n, 3, seed=7)
+    flags = bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY
+    y = run_btmv(t_orth, x, n, 3, precision, 0, flags, par)
+    ref = OE.embed_matvec(W.orthant_to_full(t_orth, par), round_input(x, precision))
+    assert rel(y, ref) <= TOL[precision]
+    # the same generator without any symmetry flag gives the same product
+    y2 = run_btmv(W.orthant_to_full(t_orth, par), x, n, 3, precision, 0)
+    assert rel(y2, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("n", [(5, 6, 7), (16, 16, 16)])
+def test_skew_parity(n):
+    t_orth, par = W.skew_orthant(n, seed=5)
+    x = W.random_vector(n, 3, seed=8)
+    y = run_btmv(t_orth, x, n, 3, 0, 0, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+    tf = W.orthant_to_full(t_orth, par)
+    ref = OE.embed_matvec(tf, round_input(x, 0))
+    assert rel(y, ref) <= 1e-5
+    # skew: x^T T x = 0
+    xr = round_input(x, 0)
+    assert abs(np.sum(xr * y)) <= 1e-5 * np.linalg.norm(xr) * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("n,par", [((6, 7), [[[1, -1]]]), ((5, 4, 6), [[[-1, 1, -1]]])])
+def test_scalar_mixed_parity(n, par):
+    par = np.array(par, dtype=np.int8)
+    t = W.random_parity_orthant(n, 1, 9, par, block_sym=False)
+    x = W.random_vector(n, 1, seed=10)
+    for precision in (0, 1):
+        y = run_btmv(t, x, n, 1, precision, 0, bt.BTMV_SYM_PARITY, par)
+        ref = OE.embed_matvec(W.orthant_to_full(t, par), round_input(x, precision))
+        assert rel(y, ref) <= TOL[precision]
+
+
+def test_block_symmetric_unstructured_c3():
+    n = (9, 10)
+    t = W.random_generator(n, 3, seed=11)
+    t = 0.5 * (t + np.swapaxes(t, 0, 1))
+    x = W.random_vector(n, 3, seed=12, nrhs=3)
+    for precision in (0, 1):
+        y = run_btmv(t, x, n, 3, precision, 0, bt.BTMV_SYM_BLOCK)
+        ref = OE.embed_matvec(t, round_input(x, precision))
+        assert rel(y, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("n,c,flags", [((6, 5), 1, 0), ((4, 3, 5), 3, 0), ((6, 5, 4), 3, 3)])
+def test_symbol_store_matches_oracle_symbol(n, c, flags):
+    """Leaf parts S_b[j] = S[2j + b] (Sec. II.C) as stored on the device."""
+    d = len(n)
+    if flags & bt.BTMV_SYM_PARITY:
+        t_in, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+        tf = W.orthant_to_full(t_in, par)
+    else:
+        t_in, par = W.random_generator(n, c, seed=13), None
+        tf = t_in
+    S = OE.symbol(tf)
+    for precision in (0, 1):
+        plan = bt.Plan(n, c, precision)
+        plan.set_kernel(t_in, flags, par)
+        info = plan.info
+        got = bt.btmv_get_symbol(plan.handle)
+        plan.close()
+        nsym = info["nsym"]
+        blocks = [(a, a) for a in range(c)] + [(a, b) for a in range(c) for b in range(a + 1, c)] \
+            if flags & bt.BTMV_SYM_BLOCK else [(a, b) for a in range(c) for b in range(c)]
+        exp = []
+        for cls in range(1 << d):
+            bits = [(cls >> (d - 1 - m)) & 1 for m in range(d)]
+            J = [((n[m] - bits[m]) // 2 + 1) if info["compressed"] else n[m] for m in range(d)]
+            for (a, b) in blocks[:nsym]:
+                sl = tuple(slice(bits[m], bits[m] + 2 * J[m], 2) for m in range(d))
+                exp.append(S[(a, b) + sl].ravel())
+        exp = np.concatenate(exp)
+        assert got.shape == exp.shape
+        assert rel(got.astype(np.complex128), exp) <= (1e-7 if precision == 0 else 1e-14)
+
+
+def test_multi_rhs_and_host_pointers():
+    n, c, r = (10, 12, 6), 3, 5
+    t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    x = W.random_vector(n, c, seed=14, nrhs=r)
+    tf = W.orthant_to_full(t_orth, par)
+    flags = bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY
+    for precision in (0, 1):
+        ref = OE.embed_matvec(tf, round_input(x, precision))
+        yd = run_btmv(t_orth, x, n, c, precision, 0, flags, par)
+        yh = run_btmv(t_orth, x, n, c, precision, 0, flags, par, host=True)
+        assert rel(yd, ref) <= TOL[precision]
+        assert rel(yh, ref) <= TOL[precision]
+        # each rhs independently equals its single-rhs product
+        y1 = run_btmv(t_orth, x[2:3], n, c, precision, 0, flags, par)
+        assert rel(yd[2:3], y1) <= TOL[precision]
+
+
+def test_errors_and_noop():
+    n = (8, 8)
+    plan = bt.Plan(n, 1, 0)
+    xd = torch.zeros((1, 1) + n, dtype=torch.complex64, device="cuda")
+    yd = torch.zeros_like(xd)
+    with pytest.raises(bt.BtmvError) as ei:
+        plan.apply(xd, yd, 1)
+    assert ei.value.status == bt.BTMV_E_STATE
+    plan.set_kernel(W.random_generator(n, 1, seed=1))
+    plan.apply(xd, yd, 0)                       # nrhs = 0: no-op
+    with pytest.raises(bt.BtmvError) as ei:
+        bt.btmv_apply(plan.handle, xd, xd, 1)   # x and y alias
+    assert ei.value.status == bt.BTMV_E_ARG
+    with pytest.raises(bt.BtmvError) as ei:
+        plan.apply(xd, yd, 2)                   # more rhs than planned
+    assert ei.value.status == bt.BTMV_E_ARG
+    plan.close()
