@@ -1,0 +1,453 @@
+#!/usr/bin/env python
+"""Block Toeplitz matvec benchmark on GB300: split FFT (Algorithm 1) vs the
+plain full circulant embedding.
+
+Default workload: d = 3, 128^3 grid, c = 3 dyadic Green blocks
+(kh = 2 pi / 20, fully symmetric, mirror-compressed symbol), complex64, one
+right-hand side.  One step = one btmv_apply (every pass of the path) on
+device-resident inputs.  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): every rank runs its own independent instance (weak
+scaling, no data-path collective); a barrier brackets the timed region and
+the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "d3_128_c3_green_c64"
+L2_BYTES = 129 * 1024 * 1024
+METRIC = "block Toeplitz matvecs/s (split FFT, d=3 128^3 c=3 Green, complex64)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--no-compare", action="store_true", help="skip the full-embedding and cuFFT rows")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2406_17981_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_kind: str, workload: str):
+    """DRAM bytes per launch recorded by ncu for this kernel (profiles/),
+    or None when absent or taken on other sources."""
+    path = os.path.join(ROOT, "profiles", f"ncu_{kernel_kind}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m1 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m2 = re.search(r"sources_sha256:\s*([0-9a-f]+)", txt)
+    if not m1 or not m2 or m2.group(1) != source_sha():
+        return None
+    return float(m1.group(1))
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), power=float(f[3]),
+                                 hw=f[5], hwt=f[6], swt=f[7], swp=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        load = [r for r in rows if r["power"] > 300] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load),
+                "sm_max_mhz": max(r["smax"] for r in rows),
+                "samples": len(load), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_generator(cfg):
+    n = cfg["n"]
+    if cfg["kind"] == "green":
+        t, par = W.green_dyadic_orthant(n, kh=cfg["kh"])
+        return t, par, 1 | 2
+    if cfg["kind"] == "skew":
+        t, par = W.skew_orthant(n, seed=cfg["t_seed"])
+        return t, par, 1 | 2
+    return W.random_generator(n, cfg["c"], seed=cfg["t_seed"]), None, 0
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, cfg):
+    """The FP64 CPU oracle as it stands, on a bounded sample: each step
+    evaluates the direct sum (the definition) at a fixed set of output points,
+    all components; the rate is scaled to matvecs/s by points / grid size."""
+    from oracle import toeplitz as OT
+    n, c = cfg["n"], cfg["c"]
+    s = int(np.prod(n))
+    t, par, _ = make_generator(cfg)
+    tf = W.orthant_to_full(t, par) if par is not None else t
+    x = W.random_vector(n, c, seed=cfg["x_seed"])
+    rng = np.random.default_rng(17)
+    t0 = time.perf_counter()
+    OT.direct_points(tf, x, [tuple(int(v) for v in rng.integers(0, n))])
+    per_pt = time.perf_counter() - t0
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    npts = max(1, int(budget / max(per_pt, 1e-6)))
+    pts = [tuple(int(v) for v in rng.integers(0, n)) for _ in range(npts)]
+    for _ in range(args.warmup):
+        OT.direct_points(tf, x, pts)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        OT.direct_points(tf, x, pts)
+    el = time.perf_counter() - t0
+    value = args.steps * npts / s / el
+    cores = len(os.sched_getaffinity(0))
+    unit = "matvecs/s"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "d": len(n), "n": list(n), "c": c,
+                                            "nrhs": 1, "sample_points_per_step": npts},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                             "sample": f"direct sum (definition, FP64 NumPy) at {npts} output points x {c} "
+                                       f"components per step, scaled by points / {s}"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    cfg = W.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args, cfg)
+        return
+
+    import torch
+
+    from paper_2406_17981_gb300 import analysis as A
+    from paper_2406_17981_gb300 import btmv as bt
+
+    ws, rank, local = dist_setup(args)
+    n, c = cfg["n"], cfg["c"]
+    prec = bt.BTMV_C64 if cfg["precision"] == "c64" else bt.BTMV_C128
+    cdt = torch.complex64 if prec == bt.BTMV_C64 else torch.complex128
+    esz = 8 if prec == bt.BTMV_C64 else 16
+    t, par, sflags = make_generator(cfg)
+    x_host = W.random_vector(n, c, seed=cfg["x_seed"])
+    xc = x_host.astype(np.complex64 if prec == bt.BTMV_C64 else np.complex128)
+
+    plan = bt.Plan(n, c, prec, bt.BTMV_ALGO_SPLIT, max_rhs=1, flags=bt.BTMV_FLAG_PROFILE)
+    plan.set_kernel(t, sflags, par)
+    info = plan.info
+    V = info["vector_bytes"]
+    # rotate over a pool of inputs/outputs so that no step finds its x in L2
+    npool = max(2, math.ceil(2 * L2_BYTES / (2 * V)) + 1)
+    xs = [torch.from_numpy(xc).to("cuda") for _ in range(npool)]
+    ys = [torch.empty_like(xs[0]) for _ in range(npool)]
+    for i in range(args.warmup):
+        plan.apply(xs[i % npool], ys[i % npool], 1)
+    torch.cuda.synchronize()
+    bt.btmv_profile_read(plan.handle)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        plan.apply(xs[i % npool], ys[i % npool], 1)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, ws)
+    prof = bt.btmv_profile_read(plan.handle)
+    value = ws * args.steps / (ms_max / 1000.0)
+    launches = info["launches_per_apply"] * args.steps
+
+    # dominant kernel and its roofline (algorithmic bytes per launch / event time)
+    sym_b = info["symbol_bytes"]
+    pb = A.split_pass_bytes(n, c, 1, esz, sym_b)
+    kind_bytes = {"fwd_split": pb["fwd_split"], "leaf": pb["leaf"], "merge": pb["bwd_merge"]}
+    dom = max((k for k in kind_bytes if prof[k][1] > 0), key=lambda k: prof[k][0])
+    per_apply_launches = prof[dom][1] / args.steps
+    bytes_per_launch = kind_bytes[dom] / per_apply_launches
+    avg_launch_s = prof[dom][0] / prof[dom][1] / 1000.0
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    kernels = {k: {"launches_per_step": prof[k][1] / args.steps, "avg_us": 1000 * prof[k][0] / prof[k][1],
+                   "share": prof[k][0] / max(1e-12, sum(v[0] for v in prof.values())),
+                   "algo_GBps": (kind_bytes[k] / (prof[k][1] / args.steps)) / (prof[k][0] / prof[k][1] / 1000) / 1e9}
+               for k in kind_bytes if prof[k][1] > 0}
+    whole_GBps = pb["total"] * args.steps / (ms / 1000.0) / 1e9
+
+    # end to end: host buffers through the public call (H2D + compute + D2H)
+    e2e = None
+    if True:
+        xh = torch.from_numpy(xc).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        ne = max(3, min(args.steps, 200))
+        for _ in range(2):
+            bt.btmv_apply(plan.handle, xh, yh, 1)
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            bt.btmv_apply(plan.handle, xh, yh, 1)   # synchronous with host pointers
+        el = max_over_ranks(time.perf_counter() - t0, ws)
+        e2e = {"value": ws * ne / el, "unit": "matvecs/s", "h2d_bytes_per_step": V, "d2h_bytes_per_step": V,
+               "steps": ne}
+
+    extra = {}
+    cpu = None
+    if rank == 0:
+        y_gpu = ys[(args.steps - 1) % npool].cpu().numpy().astype(np.complex128)
+        if not args.no_cpu:
+            from oracle import embed as OE
+            tf = W.orthant_to_full(t, par) if par is not None else t
+            cores = len(os.sched_getaffinity(0))
+            t0 = time.perf_counter()
+            ref = OE.embed_matvec(tf, xc.astype(np.complex128), workers=cores)
+            el = time.perf_counter() - t0
+            cpu = {"value": 1.0 / el, "unit": "matvecs/s", "cores": cores, "kind": "oracle",
+                   "sample": f"one full matvec of the {args.workload} workload by the FP64 oracle "
+                             f"(circulant embedding, scipy.fft, {cores} workers), {el:.1f} s"}
+            extra["rel_l2_vs_fp64_oracle"] = float(np.linalg.norm(y_gpu - ref) / np.linalg.norm(ref))
+        extra["peak_hbm_split_bytes"] = info["symbol_bytes"] + info["workspace_bytes"] + info["table_bytes"] + 2 * V
+        if not args.no_compare:
+            extra.update(compare_full(args, cfg, t, par, sflags, xc, prec, cdt, V, esz, info))
+            full = extra["full_embedding_own"]
+            extra["speedup_split_vs_full_own"] = full["ms_per_step"] / (ms_max / args.steps)
+            extra["peak_hbm_ratio_full_over_split"] = full["peak_hbm_bytes"] / extra["peak_hbm_split_bytes"]
+            cf = extra.get("full_embedding_cufft", {})
+            if "ms_per_step" in cf:
+                extra["speedup_split_vs_cufft_full"] = cf["ms_per_step"] / (ms_max / args.steps)
+    del plan
+    barrier(ws)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == bt.BTMV_C64 else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "d": len(n), "n": list(n), "c": c, "nrhs": 1,
+                   "precision": cfg["precision"], "algo": "split (Algorithm 1, depth-first)",
+                   "symbol": "compressed parity + block symmetric" if sflags == 3 else "full",
+                   "l2": f"inputs rotated over {npool} x/y pairs ({npool * 2 * V / 2**20:.0f} MiB) "
+                         f"+ {info['workspace_bytes'] / 2**20:.0f} MiB workspace + "
+                         f"{info['symbol_bytes'] / 2**20:.0f} MiB symbol, larger than the 129 MB L2",
+                   "parallelism": f"{ws} independent instance(s), one per GPU"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
+                     "traffic": ncu_traffic(dom, args.workload),
+                     "algorithmic_bytes_per_launch": bytes_per_launch},
+        "whole_step_algo_GBps": whole_GBps,
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    line.update(extra)
+    print(json.dumps(line))
+
+
+def compare_full(args, cfg, t, par, sflags, xc, prec, cdt, V, esz, info_split):
+    """The plain full embedding: own kernels, and cuFFT through torch.fft."""
+    import torch
+
+    from paper_2406_17981_gb300 import analysis as A
+    from paper_2406_17981_gb300 import btmv as bt
+    n, c = cfg["n"], cfg["c"]
+    out = {}
+    steps = max(10, min(args.steps, 200))
+    fp = bt.Plan(n, c, prec, bt.BTMV_ALGO_FULL, max_rhs=1, flags=bt.BTMV_FLAG_PROFILE)
+    fp.set_kernel(t, sflags, par)
+    finfo = fp.info
+    sym_store = bt.btmv_get_symbol(fp.handle)
+    x = torch.from_numpy(xc).cuda()
+    y = torch.empty_like(x)
+    for _ in range(3):
+        fp.apply(x, y, 1)
+    torch.cuda.synchronize()
+    bt.btmv_profile_read(fp.handle)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fp.apply(x, y, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    fb = A.full_pass_bytes(n, c, 1, esz, finfo["symbol_bytes"])
+    out["full_embedding_own"] = {
+        "matvecs_per_s": 1000.0 / ms, "ms_per_step": ms,
+        "algo_bytes_per_step": fb["total"], "algo_GBps": fb["total"] / (ms / 1000) / 1e9,
+        "peak_hbm_bytes": finfo["symbol_bytes"] + finfo["workspace_bytes"] + finfo["table_bytes"] + 2 * V}
+    del fp
+    torch.cuda.synchronize()
+    # cuFFT (torch.fft) plain embedding; its symbol is the library's own FP64
+    # build of the full 2n-grid store, interleaved back from its parity classes
+    try:
+        Sfull = torch.from_numpy(full_symbol_grid(sym_store, finfo, n, c)).cuda()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        big = tuple(2 * m for m in n)
+        scale = float(np.prod(big))
+
+        def step():
+            xp = torch.zeros((1, c) + big, dtype=cdt, device="cuda")
+            xp[(slice(None), slice(None)) + tuple(slice(0, m) for m in n)] = x
+            X = torch.fft.fftn(xp, dim=(2, 3, 4)[:len(n)])
+            Y = torch.einsum("ab...,rb...->ra...", Sfull, X) * scale
+            yy = torch.fft.ifftn(Y, dim=(2, 3, 4)[:len(n)])
+            return yy[(slice(None), slice(None)) + tuple(slice(0, m) for m in n)].contiguous()
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        csteps = max(5, min(args.steps, 50))
+        e0.record()
+        for _ in range(csteps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1) / csteps
+        out["full_embedding_cufft"] = {"matvecs_per_s": 1000.0 / cms, "ms_per_step": cms,
+                                       "peak_hbm_bytes": torch.cuda.max_memory_allocated() - base
+                                       + Sfull.numel() * Sfull.element_size()}
+        del Sfull
+    except Exception as ex:  # report, never fail the bench line
+        out["full_embedding_cufft"] = {"error": str(ex)[:200]}
+    return out
+
+
+def full_symbol_grid(store, info, n, c):
+    """[c][c][2n_1..2n_d] symbol from a full (uncompressed) class-major store:
+    class b holds S[2 j + b] for j < n (the layout btmv_get_symbol documents)."""
+    d = len(n)
+    nsym = info["nsym"]
+    blocks = ([(a, a) for a in range(c)] + [(a, b) for a in range(c) for b in range(a + 1, c)]
+              if nsym == c * (c + 1) // 2 and c > 1 else [(a, b) for a in range(c) for b in range(c)])
+    out = np.zeros((c, c) + tuple(2 * m for m in n), dtype=store.dtype)
+    s = int(np.prod(n))
+    off = 0
+    for cls in range(1 << d):
+        bits = [(cls >> (d - 1 - m)) & 1 for m in range(d)]
+        sl = tuple(slice(bits[m], None, 2) for m in range(d))
+        for k in range(nsym):
+            a, b = blocks[k]
+            blk = store[off:off + s].reshape(n)
+            out[(a, b) + sl] = blk
+            out[(b, a) + sl] = blk
+            off += s
+    return out
+
+
+if __name__ == "__main__":
+    main()

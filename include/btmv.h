@@ -82,8 +82,11 @@ enum {
 /* plan flags for btmv_plan_create (may be OR-ed) */
 enum {
   BTMV_FLAG_NONE = 0,
-  BTMV_FLAG_PROFILE = 1u << 0  /* record a CUDA event pair around every kernel
+  BTMV_FLAG_PROFILE = 1u << 0, /* record a CUDA event pair around every kernel
                                   launch of btmv_apply (see btmv_profile_read) */
+  BTMV_FLAG_GENERIC = 1u << 1  /* use only the generic shared-memory line kernels
+                                  (any 7-smooth size, both precisions) instead of
+                                  the register-resident power-of-two kernels   */
 };
 
 /*

@@ -88,19 +88,21 @@ def direct_matvec(t: np.ndarray, x: np.ndarray) -> np.ndarray:
 def direct_points(t: np.ndarray, x: np.ndarray, points) -> np.ndarray:
     """y_a[i] for the listed output points i (all components, all RHS).
 
-    For a fixed i, the offsets i - j over the grid j form the box
-    [i - (n-1), i] whose storage indices are i_m + n_m - 1 - j_m, so the
-    coefficient box is a reversed slice of t.  Returns [npts][r][c].
+    With the summation index reflected, j = n - 1 - j', the offset i - j has
+    storage index i + j' (+ n - 1 - (n - 1)), so for a fixed i the
+    coefficients form the forward box t[:, :, i : i + n] and the vector is
+    read reflected: y_a[i] = sum_b sum_j' t_ab[i + j'] x_b[n - 1 - j'].
+    Returns [npts][r][c].
     """
     c = t.shape[0]
     n = grid_shape(t)
     d = len(n)
     xs, single = _as_rhs(x, c, d)
+    xr = np.ascontiguousarray(xs[(slice(None), slice(None)) + (slice(None, None, -1),) * d])
     out = np.zeros((len(points), xs.shape[0], c), dtype=np.complex128)
+    letters = "ijklmn"[:d]
+    expr = f"ab{letters},rb{letters}->ra"
     for k, i in enumerate(points):
-        sl = tuple(slice(i[m], i[m] + n[m]) for m in range(d))
-        box = t[(slice(None), slice(None)) + sl]
-        box = box[(slice(None), slice(None)) + (slice(None, None, -1),) * d]   # index j
-        # sum over b and every grid point j
-        out[k] = xs.reshape(xs.shape[0], -1) @ np.ascontiguousarray(box).reshape(c, -1).T
+        box = t[(slice(None), slice(None)) + tuple(slice(i[m], i[m] + n[m]) for m in range(d))]
+        out[k] = np.einsum(expr, box, xr)
     return out[:, 0] if single else out

@@ -178,7 +178,7 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
   if (precision != BTMV_C64 && precision != BTMV_C128) return fail(BTMV_E_ARG, "plan_create: bad precision %d", precision);
   if (algo != BTMV_ALGO_SPLIT && algo != BTMV_ALGO_FULL) return fail(BTMV_E_ARG, "plan_create: bad algo %d", algo);
   if (max_rhs < 1) return fail(BTMV_E_ARG, "plan_create: max_rhs=%d < 1", max_rhs);
-  if (flags & ~(uint32_t)BTMV_FLAG_PROFILE) return fail(BTMV_E_ARG, "plan_create: unknown flags 0x%x", flags);
+  if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC)) return fail(BTMV_E_ARG, "plan_create: unknown flags 0x%x", flags);
   for (int m = 0; m < d; ++m) {
     if (n[m] < 1) return fail(BTMV_E_ARG, "plan_create: n[%d]=%d < 1", m, n[m]);
     const int N = algo == BTMV_ALGO_FULL ? 2 * n[m] : n[m];
@@ -435,6 +435,14 @@ static void choose_tile(PassGeom& g, size_t esz) {
   while (TL > 1 && pass_smem_bytes(g, esz) > 64 * 1024) { TL /= 2; g.TL = TL; }
 }
 
+// Register-resident kernels where the geometry allows, else the generic
+// shared-memory kernels (or always the generic ones with BTMV_FLAG_GENERIC).
+template <class T>
+static cudaError_t run_pass(btmv_plan p, int mode, const PassArgs& pa, cudaStream_t st) {
+  if (!(p->flags & BTMV_FLAG_GENERIC) && pass_reg_supported(pa, sizeof(T))) return launch_pass_reg(mode, pa, st);
+  return launch_pass<T>(mode, pa, st);
+}
+
 template <class T>
 static btmv_status split_pass(btmv_plan p, int mode, int m, int nrhs, const void* in0, const void* in1,
                               void* out0, void* out1, cudaStream_t st) {
@@ -451,7 +459,7 @@ static btmv_status split_pass(btmv_plan p, int mode, int m, int nrhs, const void
   pa.in0 = in0; pa.in1 = in1; pa.out0 = out0; pa.out1 = out1;
   pa.fft = p->fft_apply[m];
   ProfScope ps(p, mode == 0 ? BTMV_K_FWD_SPLIT : BTMV_K_MERGE, st);
-  cudaError_t e = launch_pass<T>(mode, pa, st);
+  cudaError_t e = run_pass<T>(p, mode, pa, st);
   if (e != cudaSuccess) return fail(BTMV_E_CUDA, "split pass (dim %d, mode %d): %s", m, mode, cudaGetErrorString(e));
   return BTMV_OK;
 }
@@ -488,7 +496,8 @@ static btmv_status leaf_launch(btmv_plan p, int nrhs, int nn, const LeafNode* no
   la.fft = p->fft_apply[d - 1];
   la.sym = p->symdev;
   ProfScope ps(p, full ? BTMV_K_FULL_LEAF : BTMV_K_LEAF, st);
-  cudaError_t e = launch_leaf<T>(la, st);
+  cudaError_t e = (!(p->flags & BTMV_FLAG_GENERIC) && leaf_reg_supported(la, sizeof(T))) ? launch_leaf_reg(la, st)
+                                                                                         : launch_leaf<T>(la, st);
   if (e != cudaSuccess) return fail(BTMV_E_CUDA, "leaf pass: %s", cudaGetErrorString(e));
   return BTMV_OK;
 }
@@ -596,7 +605,7 @@ static btmv_status full_apply(btmv_plan p, const void* x, void* y, int nrhs, cud
     pa.in0 = Z; pa.out0 = Z;
     pa.fft = p->fft_apply[m];
     ProfScope ps(p, mode == 0 ? BTMV_K_FULL_FWD : BTMV_K_FULL_INV, st);
-    cudaError_t e = launch_pass<T>(mode, pa, st);
+    cudaError_t e = run_pass<T>(p, mode, pa, st);
     if (e != cudaSuccess) return fail(BTMV_E_CUDA, "full pass dim %d: %s", m, cudaGetErrorString(e));
     return BTMV_OK;
   };

@@ -113,6 +113,13 @@ template <class T> cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t st);
 cudaError_t launch_fold(const FoldArgs& a, cudaStream_t st);
 cudaError_t launch_store(const StoreArgs& a, cudaStream_t st);
 
+// register-resident kernels for power-of-two lines (complex64); the
+// *_supported checks say whether a launch can take them.
+bool pass_reg_supported(const PassArgs& a, size_t esz);
+cudaError_t launch_pass_reg(int mode, const PassArgs& a, cudaStream_t st);
+bool leaf_reg_supported(const LeafArgs& a, size_t esz);
+cudaError_t launch_leaf_reg(const LeafArgs& a, cudaStream_t st);
+
 size_t pass_smem_bytes(const PassGeom& g, size_t esz);
 size_t leaf_smem_bytes(int N, int c, int rq, int Lt, size_t esz);
 

@@ -168,3 +168,30 @@ def test_errors_and_noop():
         plan.apply(xd, yd, 2)                   # more rhs than planned
     assert ei.value.status == bt.BTMV_E_ARG
     plan.close()
+
+
+REG_SIZES = [(32,), (64,), (128,), (256,), (512,), (32, 64), (8, 256), (512, 8), (64, 32, 128),
+             (16, 32, 64), (3, 128, 5), (128, 128, 16)]
+
+
+@pytest.mark.parametrize("n", REG_SIZES)
+@pytest.mark.parametrize("c", [1, 3])
+@pytest.mark.parametrize("algo", [0, 1])
+def test_register_kernels_vs_oracle_and_generic(n, c, algo):
+    """Power-of-two lines take the register-resident kernels; they must agree
+    with the oracle and with the generic shared-memory kernels."""
+    t = W.random_generator(n, c, seed=300 + sum(n))
+    x = W.random_vector(n, c, seed=301, nrhs=2)
+    y = run_btmv(t, x, n, c, 0, algo)
+    ref = OE.embed_matvec(t, round_input(x, 0))
+    assert rel(y, ref) <= 1e-5
+    plan = bt.Plan(n, c, 0, algo, max_rhs=2, flags=bt.BTMV_FLAG_GENERIC)
+    plan.set_kernel(t)
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    yd = torch.zeros_like(xd)
+    plan.apply(xd, yd, 2)
+    torch.cuda.synchronize()
+    plan.close()
+    yg = yd.cpu().numpy().astype(np.complex128)
+    assert rel(yg, ref) <= 1e-5
+    assert rel(y, yg) <= 2e-6
