@@ -156,6 +156,38 @@ BTMV_API btmv_status btmv_apply(btmv_plan p, const void* x, void* y, int nrhs, v
 BTMV_API btmv_status btmv_apply_batched(int count, const btmv_plan* plans, const void* const* x,
                                void* const* y, const int* nrhs, void* stream);
 
+/*
+ * btmv_apply_host_noalloc -- y = T x with x and y in HOST memory, like
+ * btmv_apply with host pointers, but without allocating anything.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot let the library allocate device memory when they call it.
+ * btmv_apply with host pointers allocates two staging buffers (cudaMalloc) on
+ * its first such call; a process whose device memory is reserved by another
+ * allocator, or a solver loop that must not enter the driver's allocation
+ * path, cannot accept that.  This call stages x and y through a fixed array
+ * compiled into the library instead (2 x BTMV_NOALLOC_MAX_BYTES of device
+ * memory that every GPU loading the library holds until the process exits)
+ * and calls no cudaMalloc, cudaFree or allocating library routine.
+ *   p, nrhs   as btmv_apply; the plan (symbol, tables, workspace) is created
+ *             beforehand and is only read here.
+ *   x, y      host pointers to [nrhs][c][n_1]..[n_d] complex; x is read, y is
+ *             overwritten.
+ *   stream    the copies and kernels are enqueued on it and the call
+ *             synchronises it before returning.
+ * Limit: nrhs * c * prod(n) * element size <= BTMV_NOALLOC_MAX_BYTES, else
+ * BTMV_E_UNSUPPORTED with a message (use btmv_apply then).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array,
+ * whose contents persist between calls (no call reads what an earlier one
+ * left there); calls whose work overlaps on the same GPU (other host threads
+ * or streams) race on it and must be serialised by the caller.
+ * Errors: as btmv_apply, plus BTMV_E_UNSUPPORTED for the size limit.
+ */
+#define BTMV_NOALLOC_MAX_BYTES (16u << 20)
+BTMV_API btmv_status btmv_apply_host_noalloc(btmv_plan p, const void* x, void* y, int nrhs, void* stream);
+
 /* btmv_destroy -- free every device and host resource of the plan (NULL ok).
  * Synchronises the device work of the plan first. */
 BTMV_API btmv_status btmv_destroy(btmv_plan p);

@@ -56,6 +56,7 @@ def lib() -> ctypes.CDLL:
         L.btmv_plan_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(ctypes.c_int32), i32, i32, i32, i32, u32]
         L.btmv_set_kernel.argtypes = [vp, ctypes.POINTER(ctypes.c_double), u32, ctypes.POINTER(ctypes.c_int8), vp]
         L.btmv_apply.argtypes = [vp, vp, vp, i32, vp]
+        L.btmv_apply_host_noalloc.argtypes = [vp, vp, vp, i32, vp]
         L.btmv_apply_batched.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                          ctypes.POINTER(ctypes.c_int), vp]
         L.btmv_destroy.argtypes = [vp]
@@ -64,7 +65,8 @@ def lib() -> ctypes.CDLL:
         L.btmv_plan_get_info.argtypes = [vp, ctypes.POINTER(btmv_plan_info_t)]
         L.btmv_get_symbol.argtypes = [vp, vp, ctypes.c_size_t]
         L.btmv_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
-        for name in ("btmv_plan_create", "btmv_set_kernel", "btmv_apply", "btmv_apply_batched",
+        for name in ("btmv_plan_create", "btmv_set_kernel", "btmv_apply", "btmv_apply_host_noalloc",
+                     "btmv_apply_batched",
                      "btmv_destroy", "btmv_plan_get_info", "btmv_get_symbol", "btmv_profile_read"):
             getattr(L, name).restype = st
         _lib = L
@@ -123,6 +125,12 @@ def btmv_set_kernel(plan, t: np.ndarray, sym_flags=BTMV_SYM_NONE, parity=None, s
 
 def btmv_apply(plan, x, y, nrhs, stream=None):
     _check(lib().btmv_apply(plan, _ptr(x), _ptr(y), int(nrhs), _stream(stream)))
+
+
+def btmv_apply_host_noalloc(plan, x, y, nrhs, stream=None):
+    """y = T x for host x, y staged through the library's fixed device array
+    (no device allocation; see include/btmv.h for the size limit)."""
+    _check(lib().btmv_apply_host_noalloc(plan, _ptr(x), _ptr(y), int(nrhs), _stream(stream)))
 
 
 def btmv_apply_batched(plans, xs, ys, nrhs, stream=None):

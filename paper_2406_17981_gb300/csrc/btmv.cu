@@ -670,6 +670,18 @@ static btmv_status check_apply(btmv_plan p, const void* x, void* y, int nrhs) {
   return BTMV_OK;
 }
 
+// Hooks for entry points defined in other translation units of the library
+// (not exported): argument checks, vector size, and the device-pointer apply.
+btmv_status btmv_check_apply_args(btmv_plan p, const void* x, void* y, int nrhs) {
+  return check_apply(p, x, y, nrhs);
+}
+size_t btmv_apply_vector_bytes(btmv_plan p, int nrhs) { return (size_t)nrhs * p->c * p->s * p->esz; }
+btmv_status btmv_apply_on_device(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
+  p->launches = 0;
+  return apply_device(p, x, y, nrhs, st);
+}
+btmv_status btmv_set_error(btmv_status st, const char* msg) { return fail(st, "%s", msg); }
+
 extern "C" btmv_status btmv_apply(btmv_plan p, const void* x, void* y, int nrhs, void* stream) {
   g_err.clear();
   TRY(check_apply(p, x, y, nrhs));
