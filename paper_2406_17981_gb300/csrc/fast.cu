@@ -10,9 +10,9 @@
 //
 //   k_pass_reg<P, 0>  forward split pass (even and odd children of a node)
 //   k_pass_reg<P, 1>  merge pass (IFFT(even) + conj(P) IFFT(odd))
-//   k_leaf_reg<P, C>  leaf pass: both halves of the last level, symbol
-//                     multiply, merge; the two halves run in two thread
-//                     groups and are summed through shared memory.
+//   k_leaf_cg<P, C>   leaf pass: both halves of the last level, symbol
+//                     multiply, merge; one thread group per (line,
+//                     component), spectra exchanged through shared memory.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,21 +31,38 @@ typedef RP<256, 16, 16, 1> RP256;
 typedef RP<512, 16, 8, 4> RP512;
 
 // shared-memory views of one line
+// Shared-memory views of one line.  ld/st take a point index p; cyc(t, m)
+// is the address of point t + T m and ld2(t, q, r) the address of point
+// (t + T q) T + r (the stage-2 input of a two-stage plan, where R2 = T), both
+// written so that only the t-dependent part is computed at run time.
+template <int W, int TT>
 struct SmCol {            // [p][col] with W columns, col fastest
   float2* base;
-  int W;
   __device__ __forceinline__ float2 ld(int p) const { return base[p * W]; }
   __device__ __forceinline__ void st(int p, float2 v) const { base[p * W] = v; }
+  __device__ __forceinline__ float2* cyc(int t, int m) const { return base + (t * W + m * TT * W); }
+  __device__ __forceinline__ float2* ld2(int t, int q, int r) const { return base + (t * TT * W + (q * TT * TT + r) * W); }
   __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
-struct SmLine {           // one line, one pad slot every 16 points
+// One line owned by one warp-resident thread group, one pad slot every PD
+// points (PD = min(T, 16)).  With groups spaced by a stride that is T modulo
+// 16 (in 8-byte words), the stage-1 writes and stage-2 reads of all groups
+// sharing a half-warp fall into distinct banks.
+template <int PD, int TT>
+struct SmLine {
   float2* base;
-  __device__ __forceinline__ float2 ld(int p) const { return base[p + (p >> 4)]; }
-  __device__ __forceinline__ void st(int p, float2 v) const { base[p + (p >> 4)] = v; }
+  __device__ __forceinline__ float2 ld(int p) const { return base[p + p / PD]; }
+  __device__ __forceinline__ void st(int p, float2 v) const { base[p + p / PD] = v; }
+  // valid when PD == TT: point t + T m sits at t + m (T + 1)
+  __device__ __forceinline__ float2* cyc(int t, int m) const { return base + (t + m * (TT + 1)); }
+  __device__ __forceinline__ float2* ld2(int t, int q, int r) const {
+    return base + (t * (TT + 1) + q * TT * (TT + 1) + r);
+  }
   __device__ __forceinline__ void sync() const { __syncwarp(); }
 };
 
-template <class P> __host__ __device__ constexpr int padded_len() { return P::N + P::N / 16; }
+template <class P> __host__ __device__ constexpr int pad_div() { return P::T < 16 ? P::T : 16; }
+template <class P> __host__ __device__ constexpr int padded_len() { return P::N + P::N / pad_div<P>(); }
 
 // In: a[m] = v[t + T m].  Out: a[m] = DFT(v)[t + T m] (forward or inverse, unnormalised).
 template <class P, bool INV, class SM>
@@ -108,6 +125,52 @@ __device__ __forceinline__ void fft_reg(float2 (&a)[P::R1], int t, const SM& sm,
   }
 }
 
+// Stage-2 twiddles of a two-stage plan held in registers: w[q][r] =
+// exp(-2 pi i r f1 / N) for the thread's butterflies f1 = t + T q.
+template <class P>
+struct TwReg {
+  static constexpr int NQ = P::R1 / P::T > 0 ? P::R1 / P::T : 1;   // (unused by three-stage plans)
+  float2 w[NQ][P::R2];
+  __device__ __forceinline__ void load(int t, const float2* __restrict__ tw) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+      for (int r = 0; r < P::R2; ++r) w[q][r] = __ldg(&tw[r * (t + P::T * q)]);
+  }
+};
+
+// fft_reg for two-stage plans with the stage-2 twiddles already in registers.
+template <class P, bool INV, class SM>
+__device__ __forceinline__ void fft_reg2(float2 (&a)[P::R1], int t, const SM& sm, const TwReg<P>& tw) {
+  constexpr int R1 = P::R1, R2 = P::R2, TT = P::T;
+  static_assert(P::R3 == 1, "two-stage plans only");
+  static_assert(R2 == TT, "two-stage plans have R2 == T");
+  dft<R1, INV>(a);
+  sm.sync();
+#pragma unroll
+  for (int f2 = 0; f2 < R1; ++f2) *sm.cyc(t, f2) = a[f2];
+  sm.sync();
+  constexpr int NQ = R1 / TT;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    float2 b[R2];
+#pragma unroll
+    for (int r = 0; r < R2; ++r) b[r] = *sm.ld2(t, q, r);
+#pragma unroll
+    for (int r = 1; r < R2; ++r) b[r] = twm<INV>(b[r], tw.w[q][r]);
+    dft<R2, INV>(b);
+#pragma unroll
+    for (int f2 = 0; f2 < R2; ++f2) a[q + NQ * f2] = b[f2];
+  }
+}
+
+template <class P, bool INV, class SM>
+__device__ __forceinline__ void fft_any(float2 (&a)[P::R1], int t, const SM& sm, const TwReg<P>& twr,
+                                        const float2* __restrict__ tw) {
+  if constexpr (P::R3 == 1) fft_reg2<P, INV>(a, t, sm, twr);
+  else fft_reg<P, INV>(a, t, sm, tw);
+}
+
 // ------------------------------------------------------------- strided pass
 // columns per tile: 16 x 8 B = 128 B rows (8 for N = 512 to stay in 32 KB)
 template <class P> __host__ __device__ constexpr int pass_cols() { return P::N <= 256 ? 16 : 8; }
@@ -126,7 +189,9 @@ __global__ void __launch_bounds__(pass_cols<P>() * P::T) k_pass_reg(const PassAr
   const long long base = o * (long long)N * inner + ii;   // same geometry for every array
   const float2* __restrict__ tw = (const float2*)a.fft.tw;
   const float2* __restrict__ ph = (const float2*)a.fft.ph;
-  const SmCol smc{sm + col, PW};
+  const SmCol<PW, TT> smc{sm + col};
+  TwReg<P> twr;
+  if constexpr (P::R3 == 1) twr.load(t, tw);
 
   if (MODE == 0) {
     const float2* __restrict__ in = (const float2*)a.in0;
@@ -137,7 +202,7 @@ __global__ void __launch_bounds__(pass_cols<P>() * P::T) k_pass_reg(const PassAr
       float2 w[R1];
 #pragma unroll
       for (int m = 0; m < R1; ++m) w[m] = v[m];
-      fft_reg<P, false>(w, t, smc, tw);
+      fft_any<P, false>(w, t, smc, twr, tw);
       float2* __restrict__ out = (float2*)a.out0;
       if (ok)
 #pragma unroll
@@ -146,7 +211,7 @@ __global__ void __launch_bounds__(pass_cols<P>() * P::T) k_pass_reg(const PassAr
     if (a.out1) {
 #pragma unroll
       for (int m = 0; m < R1; ++m) v[m] = cmul(v[m], __ldg(&ph[t + TT * m]));
-      fft_reg<P, false>(v, t, smc, tw);
+      fft_any<P, false>(v, t, smc, twr, tw);
       float2* __restrict__ out = (float2*)a.out1;
       if (ok)
 #pragma unroll
@@ -162,9 +227,9 @@ __global__ void __launch_bounds__(pass_cols<P>() * P::T) k_pass_reg(const PassAr
 #pragma unroll
       for (int m = 0; m < R1; ++m) od[m] = ok ? ino[base + (long long)(t + TT * m) * inner] : make_float2(0.f, 0.f);
     }
-    fft_reg<P, true>(e, t, smc, tw);
+    fft_any<P, true>(e, t, smc, twr, tw);
     if (ino) {
-      fft_reg<P, true>(od, t, smc, tw);
+      fft_any<P, true>(od, t, smc, twr, tw);
 #pragma unroll
       for (int m = 0; m < R1; ++m) e[m] = cadd(e[m], cmulc(od[m], __ldg(&ph[t + TT * m])));
     }
@@ -176,56 +241,70 @@ __global__ void __launch_bounds__(pass_cols<P>() * P::T) k_pass_reg(const PassAr
 }
 
 // ------------------------------------------------------------------- leaf
-constexpr int LEAF_THREADS = 256;
+// One thread group of T threads per (line, component); a line's C groups
+// sit next to each other in the block.  Each group runs the even half, then
+// the odd half of the last level: forward FFT, spectrum to shared memory, the
+// row cc of the c x c symbol multiply (reading the other components'
+// spectra), inverse FFT.  The even result waits in a per-group stash until
+// the odd one is added with conj(P).  The plain embedding (a.split == 0)
+// runs a single 2n-point pass per line.
+template <class P, int C> struct LeafCfg {
+  // lines per block: 96 threads for c = 3, 128 for c = 1 (whole warps)
+  static constexpr int LPC = C == 1 ? 128 / P::T : 32 / P::T;
+  static constexpr int THREADS = LPC * C * P::T;
+  static constexpr int SPN = padded_len<P>();
+  static constexpr int BASE = SPN + P::N;                        // spectrum + stash
+  static constexpr int TGT = P::T < 16 ? P::T : 0;
+  static constexpr int GS = BASE + ((TGT - BASE % 16) + 16) % 16;  // group stride, = T mod 16
+  // staged symbol rows: stored block k of a line's row starts at
+  // k * JP + 8 * s(k) and lines are LS apart, chosen so that the rows two
+  // thread groups of a half-warp read together sit in opposite bank halves
+  static constexpr int JP = ((P::N / 2 + 1 + 8) + 15) / 16 * 16;
+  static __host__ __device__ constexpr int line_stride(int nsym) { return nsym * JP + 8; }
+  static constexpr int MINB = P::R3 == 1 ? (C == 1 ? 2 : 5) : 1; // blocks per SM to aim for
+  // dynamic smem: groups | phase table | staged symbol rows (nsym per line)
+  static size_t smem(int nsym) {
+    return ((size_t)LPC * C * GS + P::N + (size_t)LPC * line_stride(nsym)) * sizeof(float2);
+  }
+};
 
-// Split leaf: thread groups 2g and 2g+1 take the even and odd half of one
-// line.  Plain embedding (a.split == 0): every group takes its own 2n line.
-template <class P, int C>
-__global__ void __launch_bounds__(LEAF_THREADS) k_leaf_reg(const LeafArgs a) {
-  constexpr int R1 = P::R1, TT = P::T, N = P::N, PN = padded_len<P>();
-  constexpr int GROUPS = LEAF_THREADS / TT;
-  __shared__ float2 sm[GROUPS * PN];
-  const int gid = threadIdx.x / TT;
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <class P, int C, bool FF>
+__global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k_leaf_cg(const LeafArgs a) {
+  typedef LeafCfg<P, C> CF;
+  constexpr int R1 = P::R1, TT = P::T, N = P::N, PD = pad_div<P>(), JP = CF::JP;
+  extern __shared__ __align__(16) float2 smem_cg[];
+  const int gid = threadIdx.x / TT;           // group in block
   const int t = threadIdx.x % TT;
-  const int LPC = a.split ? GROUPS / 2 : GROUPS;   // lines per CTA
-  const int b = a.split ? (gid & 1) : 0;
-  const int li = a.split ? (gid >> 1) : gid;
-  const SmLine sml{sm + gid * PN};
-  const SmLine partner{sm + (gid ^ 1) * PN};
+  const int li = gid / C;                     // line in block
+  const int cc = gid - li * C;                // component of this group
+  const int lt = threadIdx.x - li * C * TT;   // thread index within the line
+  float2* const gbuf = smem_cg + gid * CF::GS;
+  const SmLine<PD, TT> spec{gbuf};
+  float2* const stash = gbuf + CF::SPN;
+  float2* const phs = smem_cg + CF::LPC * C * CF::GS;           // phase table P (N values)
+  const SymDev& S = a.sym;
+  float2* const rowb = phs + N + li * CF::line_stride(S.nsym);    // staged symbol row of this line
   const LeafNode nd = a.nodes[blockIdx.y];
-  const long long gline = (long long)blockIdx.x * LPC + li;  // over (rhs, line)
+  const long long gline = (long long)blockIdx.x * CF::LPC + li;   // over (rhs, line)
   const bool ok = gline < (long long)a.nrhs * a.lines;
   const long long q = ok ? gline / a.lines : 0;
   const long long line = ok ? gline - q * a.lines : 0;
-  const long long base = q * a.rhs_stride + line * N;
+  const long long base = q * a.rhs_stride + cc * a.comp_stride + line * N + t;
   const float2* __restrict__ tw = (const float2*)a.fft.tw;
   const float2* __restrict__ ph = (const float2*)a.fft.ph;
-  const float2* __restrict__ in = (const float2*)nd.in;
 
-  float2 v[C][R1];
-#pragma unroll
-  for (int c = 0; c < C; ++c)
-#pragma unroll
-    for (int m = 0; m < R1; ++m)
-      v[c][m] = ok ? in[base + c * a.comp_stride + t + TT * m] : make_float2(0.f, 0.f);
-  if (b) {
-#pragma unroll
-    for (int m = 0; m < R1; ++m) {
-      const float2 p = __ldg(&ph[t + TT * m]);
-#pragma unroll
-      for (int c = 0; c < C; ++c) v[c][m] = cmul(v[c][m], p);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < C; ++c) fft_reg<P, false>(v[c], t, sml, tw);
-
-  // symbol rows of this line for both parities of the last dim: class,
-  // fold mask and linear prefix of dims 0..d-2
-  const SymDev& S = a.sym;
+  // symbol addressing for this line
   const int dl = a.dl;
   int clsp = 0, foldp = 0;
-  int fpre[MAX_D];
+  long long lin = 0;
   {
+    int fpre[MAX_D];
     long long r = line;
     for (int m = dl - 1; m >= 0; --m) {
       const int im = (int)(r % a.ext[m]);
@@ -233,81 +312,140 @@ __global__ void __launch_bounds__(LEAF_THREADS) k_leaf_reg(const LeafArgs a) {
       fpre[m] = a.split ? 2 * im + ((nd.prefix >> m) & 1) : im;
     }
     for (int m = 0; m < dl; ++m) clsp = (clsp << 1) | (fpre[m] & 1);
-  }
-  long long lin = 0;
-  for (int m = 0; m < dl; ++m) {
-    int fm = fpre[m];
-    if (S.compressed && fm > S.n[m]) { fm = 2 * S.n[m] - fm; foldp |= 1 << m; }
-    lin = lin * S.J[clsp << 1][m] + (fm >> 1);    // J of dims < dl does not depend on the last bit
+    for (int m = 0; m < dl; ++m) {
+      int fm = fpre[m];
+      if (S.compressed && fm > S.n[m]) { fm = 2 * S.n[m] - fm; foldp |= 1 << m; }
+      lin = lin * S.J[clsp << 1][m] + (fm >> 1);
+    }
   }
   const int nl = S.n[dl];
-  long long rowc[2], blkc[2];
-#pragma unroll
-  for (int bb = 0; bb < 2; ++bb) {
-    const int cl = (clsp << 1) | bb;
-    rowc[bb] = S.cls_off[cl] + lin * S.J[cl][dl];
-    blkc[bb] = S.blk[cl];
-  }
   const float2* __restrict__ Sd = (const float2*)S.data;
-  int kk[3][3];
-#pragma unroll
-  for (int i = 0; i < C; ++i)
-#pragma unroll
-    for (int j = 0; j < C; ++j) kk[i][j] = S.comp[i][j];
+  // FF: split leaf on the mirror-compressed store with n_d == N; the line's
+  // row of each parity class is staged in shared memory while the
+  // transforms run
+  const int nsym = S.nsym;
+  // bank-half shift of each stored block of the c = 3 block-symmetric row:
+  // blocks 00 11 22 01 02 12 -> 0 0 0 1 0 1
+  auto row_pos = [&](int k) { return k * JP + ((C == 3 && nsym == 6 && (k == 3 || k == 5)) ? 8 : 0); };
+  auto stage_row = [&](int bb) {
+    if (!FF || !ok) return;
+    const int cl = (clsp << 1) | bb;
+    const int J = S.J[cl][dl];
+    const float2* src = Sd + S.cls_off[cl] + lin * J;
+    const long long blk = S.blk[cl];
+    for (int k = 0; k < nsym; ++k)
+      for (int j = lt; j < J; j += C * TT) cp_async8(rowb + row_pos(k) + j, src + k * blk + j);
+  };
+  for (int e = threadIdx.x; e < N; e += CF::THREADS) cp_async8(phs + e, ph + e);
+  stage_row(0);
 
+  TwReg<P> twr;
+  if constexpr (P::R3 == 1) twr.load(t, tw);
+
+  float2 xr[R1];
+  {
+    const float2* __restrict__ in = (const float2*)nd.in + base;
 #pragma unroll
-  for (int m = 0; m < R1; ++m) {
-    const int l = t + TT * m;
-    int f = a.split ? 2 * l + b : l;
-    int fold = foldp;
-    if (S.compressed && f > nl) { f = 2 * nl - f; fold |= 1 << dl; }
-    const int pb = f & 1;                 // parity class bit of the last dim
-    const long long idx = rowc[pb] + (f >> 1);
-    const long long blk = blkc[pb];
-    if (C == 1) {
-      float2 s = __ldg(&Sd[idx]);
-      if (__popc(S.oddmask[0] & fold) & 1) { s.x = -s.x; s.y = -s.y; }
-      v[0][m] = cmul(s, v[0][m]);
-    } else {
-      float2 x[C];
+    for (int m = 0; m < R1; ++m) xr[m] = ok ? in[TT * m] : make_float2(0.f, 0.f);
+  }
+
+  long long off[2][C];
+  int kr[C];
+  unsigned sg0 = 0, sg1 = 0;      // sign bits of row cc without / with a fold of the last dim
 #pragma unroll
-      for (int c = 0; c < C; ++c) x[c] = v[c][m];
+  for (int j = 0; j < C; ++j) {
+    const int k = S.comp[cc][j];
+    kr[j] = row_pos(k);
 #pragma unroll
-      for (int i = 0; i < C; ++i) {
+    for (int bb = 0; bb < 2; ++bb) {
+      const int cl = (clsp << 1) | bb;
+      off[bb][j] = S.cls_off[cl] + lin * S.J[cl][dl] + (long long)k * S.blk[cl];
+    }
+    sg0 |= (unsigned)(__popc(S.oddmask[k] & foldp) & 1) << j;
+    sg1 |= (unsigned)(__popc(S.oddmask[k] & (foldp | (1 << dl))) & 1) << j;
+  }
+  float sgf0[C], sgf1[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    sgf0[j] = ((sg0 >> j) & 1) ? -1.f : 1.f;
+    sgf1[j] = ((sg1 >> j) & 1) ? -1.f : 1.f;
+  }
+  float2* const lbase = smem_cg + (li * C) * CF::GS;   // spectra of this line's groups
+
+  const int nbr = a.split ? 2 : 1;
+  for (int b = 0; b < nbr; ++b) {
+    if (b) cp_async_wait_all();       // phase table staged
+    __syncthreads();
+    float2 w[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) w[m] = b ? cmul(xr[m], phs[t + TT * m]) : xr[m];
+    fft_any<P, false>(w, t, spec, twr, tw);
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < R1; ++m) {
+      if constexpr (PD == TT) *spec.cyc(t, m) = w[m];
+      else spec.st(t + TT * m, w[m]);
+    }
+    cp_async_wait_all();              // this branch's symbol row
+    __syncthreads();
+    // row cc of the symbol multiply at the thread's frequencies
+    if constexpr (FF) {
+      // frequency f = 2l + b is stored directly for l < N/2 (m < R1/2) and
+      // folded to 2N - f, index N - l - b, with the fold signs for l >= N/2
+#pragma unroll
+      for (int m = 0; m < R1; ++m) {
+        const bool hi = m >= R1 / 2;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-          const int k = kk[i][j];
-          float2 s = __ldg(&Sd[idx + k * blk]);
-          if (__popc(S.oddmask[k] & fold) & 1) { s.x = -s.x; s.y = -s.y; }
-          acc = cadd(acc, cmul(s, x[j]));
+          float2 sv = hi ? rowb[kr[j] + (N - b - t - TT * m)] : rowb[kr[j] + (t + TT * m)];
+          const float sgn = hi ? sgf1[j] : sgf0[j];
+          sv.x *= sgn; sv.y *= sgn;
+          const SmLine<PD, TT> sj{lbase + j * CF::GS};
+          const float2 xv = (PD == TT) ? *sj.cyc(t, m) : sj.ld(t + TT * m);
+          acc = cadd(acc, cmul(sv, xv));
         }
-        v[i][m] = acc;
+        w[m] = acc;
       }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < C; ++c) fft_reg<P, true>(v[c], t, sml, tw);
-
-  // merge the halves: the odd group hands conj(P) y_odd to the even group
-  float2* __restrict__ out = (float2*)nd.out;
-#pragma unroll
-  for (int c = 0; c < C; ++c) {
-    __syncthreads();
-    if (a.split && b) {
-#pragma unroll
-      for (int m = 0; m < R1; ++m) sml.st(t + TT * m, cmulc(v[c][m], __ldg(&ph[t + TT * m])));
-    }
-    __syncthreads();
-    if (!b && ok) {
+    } else {
 #pragma unroll
       for (int m = 0; m < R1; ++m) {
-        float2 y = v[c][m];
-        if (a.split) y = cadd(y, partner.ld(t + TT * m));
-        out[base + c * a.comp_stride + t + TT * m] = y;
+        const int l = t + TT * m;
+        int f = a.split ? 2 * l + b : l;
+        unsigned sg = sg0;
+        if (S.compressed && f > nl) { f = 2 * nl - f; sg = sg1; }
+        const int pb = f & 1;
+        const int fi = f >> 1;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          float2 sv = __ldg(&Sd[off[pb][j] + fi]);
+          if ((sg >> j) & 1) { sv.x = -sv.x; sv.y = -sv.y; }
+          const SmLine<PD, TT> sj{lbase + j * CF::GS};
+          acc = cadd(acc, cmul(sv, sj.ld(l)));
+        }
+        w[m] = acc;
+      }
+    }
+    __syncthreads();
+    if (b == 0 && a.split) stage_row(1);   // overlaps the inverse and the odd forward transform
+    fft_any<P, true>(w, t, spec, twr, tw);
+    if (a.split && b == 0) {
+#pragma unroll
+      for (int m = 0; m < R1; ++m) stash[t + TT * m] = w[m];
+    } else {
+      float2* __restrict__ out = (float2*)nd.out + base;
+      if (ok) {
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+          float2 y = w[m];
+          if (a.split) y = cadd(stash[t + TT * m], cmulc(y, phs[t + TT * m]));
+          out[TT * m] = y;
+        }
       }
     }
   }
+  cp_async_wait_all();
 }
 
 // ------------------------------------------------------------- dispatch
@@ -344,15 +482,28 @@ cudaError_t launch_pass_reg(int mode, const PassArgs& a, cudaStream_t st) {
   return cudaErrorNotSupported;
 }
 
+template <class P, int C, bool FF>
+static cudaError_t leaf_reg_pf(const LeafArgs& a, cudaStream_t st) {
+  typedef LeafCfg<P, C> CF;
+  const long long total = (long long)a.nrhs * a.lines;
+  const long long nt = (total + CF::LPC - 1) / CF::LPC;
+  if (nt <= 0 || a.nnodes <= 0) return cudaSuccess;
+  const size_t sm = CF::smem(FF ? a.sym.nsym : 0);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_leaf_cg<P, C, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  if (sm > 227 * 1024) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)nt, (unsigned)a.nnodes);
+  k_leaf_cg<P, C, FF><<<grid, CF::THREADS, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <class P, int C>
 static cudaError_t leaf_reg_p(const LeafArgs& a, cudaStream_t st) {
-  const int LPC = a.split ? LEAF_THREADS / P::T / 2 : LEAF_THREADS / P::T;
-  const long long total = (long long)a.nrhs * a.lines;
-  const long long nt = (total + LPC - 1) / LPC;
-  if (nt <= 0 || a.nnodes <= 0) return cudaSuccess;
-  dim3 grid((unsigned)nt, (unsigned)a.nnodes);
-  k_leaf_reg<P, C><<<grid, LEAF_THREADS, 0, st>>>(a);
-  return cudaGetLastError();
+  const bool ff = a.split && a.sym.compressed && a.sym.n[a.dl] == a.N;
+  return ff ? leaf_reg_pf<P, C, true>(a, st) : leaf_reg_pf<P, C, false>(a, st);
 }
 
 bool leaf_reg_supported(const LeafArgs& a, size_t esz) {
