@@ -148,9 +148,22 @@ BTMV_API btmv_status btmv_apply(btmv_plan p, const void* x, void* y, int nrhs, v
 
 /*
  * btmv_apply_batched -- y_k = T_k x_k for count independent plans, enqueued
- * as one unit of work on stream.
+ * as one persistent kernel launch on stream.
  *   plans, x, y, nrhs  host arrays of length count; entry k as in btmv_apply
  *                      (device pointers only).  Plans must be distinct.
+ * SPLIT plans of one precision run together in one launch of a persistent
+ * kernel: every plan's depth-first schedule (the launches btmv_apply would
+ * make) becomes a chain of stages, stages of different plans run side by
+ * side, and each wait for a previous stage is bounded (BTMV_WAIT_TIMEOUT_MS,
+ * default 5000 ms).  The launch is captured once into a CUDA graph per
+ * argument set (plans, x, y, nrhs) and replayed on later calls with the same
+ * arguments; the first call for a new set of problem shapes also times a few
+ * tile / radix choices on the caller's data and keeps the fastest (process
+ * wide, and in the file named by BTMV_TUNE_CACHE if set).  Other mixes
+ * (BTMV_ALGO_FULL plans, mixed precisions) run one apply after the other.
+ * The first call for an argument set allocates its stage table; a wait that
+ * expired in a launch is reported (BTMV_E_TIMEOUT) by the next call with the
+ * same arguments.
  * Errors: as btmv_apply; on an argument error nothing is enqueued.
  */
 BTMV_API btmv_status btmv_apply_batched(int count, const btmv_plan* plans, const void* const* x,
@@ -187,6 +200,27 @@ BTMV_API btmv_status btmv_apply_batched(int count, const btmv_plan* plans, const
  */
 #define BTMV_NOALLOC_MAX_BYTES (16u << 20)
 BTMV_API btmv_status btmv_apply_host_noalloc(btmv_plan p, const void* x, void* y, int nrhs, void* stream);
+
+/*
+ * btmv_batch_tuning -- report the tuning chosen for a batch that has run:
+ * cfg_out[0..6] = strided-pass tile lines, leaf lines per tile, leaf
+ * right-hand sides per tile, radix order (0: 16 first, 1: 8 first), stages,
+ * work items, blocks of the persistent launch.  Arguments as for the
+ * btmv_apply_batched call.  Errors: BTMV_E_ARG, BTMV_E_STATE (no such batch).
+ */
+BTMV_API btmv_status btmv_batch_tuning(int count, const btmv_plan* plans, const void* const* x,
+                                       void* const* y, const int* nrhs, int* cfg_out);
+
+/*
+ * btmv_selftest_wait_timeout -- failure-detection self test of the bounded
+ * waits of the persistent kernel: launches it with one work item whose
+ * dependency count is withheld, so that its wait expires after timeout_ms.
+ * Returns BTMV_E_TIMEOUT when the kernel detected the expired wait and
+ * returned normally (the expected outcome; the CUDA context stays usable),
+ * BTMV_E_STATE if no timeout was reported, BTMV_E_CUDA / BTMV_E_NOMEM on
+ * other failures.  Synchronises stream.
+ */
+BTMV_API btmv_status btmv_selftest_wait_timeout(int timeout_ms, void* stream);
 
 /* btmv_destroy -- free every device and host resource of the plan (NULL ok).
  * Synchronises the device work of the plan first. */

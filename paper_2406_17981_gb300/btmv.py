@@ -65,8 +65,11 @@ def lib() -> ctypes.CDLL:
         L.btmv_plan_get_info.argtypes = [vp, ctypes.POINTER(btmv_plan_info_t)]
         L.btmv_get_symbol.argtypes = [vp, vp, ctypes.c_size_t]
         L.btmv_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        L.btmv_batch_tuning.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.btmv_selftest_wait_timeout.argtypes = [i32, vp]
         for name in ("btmv_plan_create", "btmv_set_kernel", "btmv_apply", "btmv_apply_host_noalloc",
-                     "btmv_apply_batched",
+                     "btmv_apply_batched", "btmv_batch_tuning", "btmv_selftest_wait_timeout",
                      "btmv_destroy", "btmv_plan_get_info", "btmv_get_symbol", "btmv_profile_read"):
             getattr(L, name).restype = st
         _lib = L
@@ -140,6 +143,24 @@ def btmv_apply_batched(plans, xs, ys, nrhs, stream=None):
     Y = (ctypes.c_void_p * max(1, k))(*[_ptr(y) for y in ys])
     R = (ctypes.c_int * max(1, k))(*[int(r) for r in nrhs])
     _check(lib().btmv_apply_batched(k, P, X, Y, R, _stream(stream)))
+
+
+def btmv_batch_tuning(plans, xs, ys, nrhs) -> dict:
+    k = len(plans)
+    P = (ctypes.c_void_p * max(1, k))(*plans)
+    X = (ctypes.c_void_p * max(1, k))(*[_ptr(x) for x in xs])
+    Y = (ctypes.c_void_p * max(1, k))(*[_ptr(y) for y in ys])
+    R = (ctypes.c_int * max(1, k))(*[int(r) for r in nrhs])
+    out = (ctypes.c_int * 7)()
+    _check(lib().btmv_batch_tuning(k, P, X, Y, R, out))
+    keys = ("tile_lines", "leaf_lines", "leaf_rhs", "radix_order", "stages", "items", "blocks")
+    return dict(zip(keys, list(out)))
+
+
+def btmv_selftest_wait_timeout(timeout_ms=200, stream=None) -> int:
+    """Runs the bounded-wait self test; returns the status code (expected:
+    BTMV_E_TIMEOUT)."""
+    return lib().btmv_selftest_wait_timeout(int(timeout_ms), _stream(stream))
 
 
 def btmv_destroy(plan):

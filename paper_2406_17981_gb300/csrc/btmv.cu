@@ -14,13 +14,14 @@
 
 #include "../../include/btmv.h"
 #include "kernels.cuh"
+#include "plan.h"
 
 using namespace btmv;
 
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_err;
 
-static btmv_status fail(btmv_status st, const char* fmt, ...) {
+btmv_status btmv::fail(btmv_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -38,48 +39,9 @@ static btmv_status fail(btmv_status st, const char* fmt, ...) {
                   "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
   } while (0)
 
-// ------------------------------------------------------------------ plan
-struct TableSet {
-  void* mem = nullptr;                 // device
-  std::map<int, size_t> off_f, off_d;  // N -> byte offset of [tw N][ph N]
-  size_t bytes = 0;
-};
+static bool factor_radices(int N, FftDev& f) { return factor_radices_mode(N, f, 0); }
 
-struct btmv_plan_s {
-  int d = 0, c = 0, prec = 0, algo = 0, max_rhs = 0;
-  uint32_t flags = 0;
-  int n[MAX_D] = {1, 1, 1, 1};
-  long long s = 1;          // prod n
-  long long s2 = 1;         // prod 2n
-  size_t esz = 8;           // bytes per complex
-  int dev = 0;
-  TableSet tab;
-  FftDev fft_apply[MAX_D];  // per dim, plan precision (N = n_m split, 2 n_m full)
-  FftDev fft_sym[MAX_D];    // per dim, FP64, N = n_m
-  // symbol
-  void* sym = nullptr;
-  size_t sym_bytes = 0;
-  SymDev symdev;
-  bool has_sym = false;
-  int nsym = 0;
-  int compressed = 0;
-  // workspace
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  std::vector<void*> W;     // split: d-1 vectors; full: Z
-  // host staging
-  void* stage_x = nullptr;
-  void* stage_y = nullptr;
-  // profiling
-  struct Rec { int kind; cudaEvent_t a, b; };
-  std::vector<Rec> pending;
-  std::vector<cudaEvent_t> pool;
-  double acc_ms[BTMV_K_NKINDS] = {0};
-  int64_t acc_n[BTMV_K_NKINDS] = {0};
-  int launches = 0;
-};
-
-static bool factor_radices(int N, FftDev& f) {
+bool btmv::factor_radices_mode(int N, FftDev& f, int mode) {
   f.N = N;
   f.nst = 0;
   int a = 0, m = N;
@@ -90,6 +52,8 @@ static bool factor_radices(int N, FftDev& f) {
   while (m % 7 == 0) { m /= 7; ++c7; }
   if (m != 1) return false;
   std::vector<int> r;
+  if (mode == 1)
+    while (a >= 3) { r.push_back(8); a -= 3; }
   while (a >= 4) {
     if (a == 5) { r.push_back(8); r.push_back(4); a = 0; break; }
     r.push_back(16);
@@ -443,9 +407,8 @@ static cudaError_t run_pass(btmv_plan p, int mode, const PassArgs& pa, cudaStrea
   return launch_pass<T>(mode, pa, st);
 }
 
-template <class T>
-static btmv_status split_pass(btmv_plan p, int mode, int m, int nrhs, const void* in0, const void* in1,
-                              void* out0, void* out1, cudaStream_t st) {
+PassArgs btmv::split_pass_args(btmv_plan p, const Step& stp, int nrhs, size_t esz, int TL) {
+  const int m = stp.dim;
   long long outer = (long long)nrhs * p->c, inner = 1;
   for (int q = 0; q < m; ++q) outer *= p->n[q];
   for (int q = m + 1; q < p->d; ++q) inner *= p->n[q];
@@ -454,13 +417,24 @@ static btmv_status split_pass(btmv_plan p, int mode, int m, int nrhs, const void
   const int N = p->n[m];
   pa.g.N = N; pa.g.ni = inner > 1 ? 1 : 0; pa.g.I[0] = (int)inner; pa.g.Itot = inner;
   pa.g.lines = outer * inner; pa.g.contig = inner == 1;
-  choose_tile(pa.g, sizeof(T));
+  choose_tile(pa.g, esz);
+  if (TL > 0) {
+    pa.g.TL = TL;
+    while (pa.g.TL > 1 && pass_smem_bytes(pa.g, esz) > 96 * 1024) pa.g.TL /= 2;
+  }
   pa.a_in0 = pa.a_in1 = pa.a_out0 = pa.a_out1 = contig_map(N, inner);
-  pa.in0 = in0; pa.in1 = in1; pa.out0 = out0; pa.out1 = out1;
+  pa.in0 = stp.in0; pa.in1 = stp.in1; pa.out0 = stp.out0; pa.out1 = stp.out1;
   pa.fft = p->fft_apply[m];
+  return pa;
+}
+
+template <class T>
+static btmv_status split_pass(btmv_plan p, const Step& stp, int nrhs, cudaStream_t st) {
+  const int mode = stp.kind;
+  PassArgs pa = split_pass_args(p, stp, nrhs, sizeof(T), 0);
   ProfScope ps(p, mode == 0 ? BTMV_K_FWD_SPLIT : BTMV_K_MERGE, st);
   cudaError_t e = run_pass<T>(p, mode, pa, st);
-  if (e != cudaSuccess) return fail(BTMV_E_CUDA, "split pass (dim %d, mode %d): %s", m, mode, cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(BTMV_E_CUDA, "split pass (dim %d, mode %d): %s", stp.dim, mode, cudaGetErrorString(e));
   return BTMV_OK;
 }
 
@@ -472,9 +446,8 @@ static void leaf_tiling(int N, int c, int nrhs, size_t esz, int& rq, int& Lt) {
   (void)nrhs;
 }
 
-template <class T>
-static btmv_status leaf_launch(btmv_plan p, int nrhs, int nn, const LeafNode* nodes, bool full,
-                               cudaStream_t st) {
+LeafArgs btmv::leaf_step_args(btmv_plan p, int nrhs, int nn, const LeafNode* nodes, bool full, size_t esz, int Lt,
+                              int rq) {
   LeafArgs la;
   memset(&la, 0, sizeof la);
   const int d = p->d;
@@ -487,7 +460,12 @@ static btmv_status leaf_launch(btmv_plan p, int nrhs, int nn, const LeafNode* no
   la.comp_stride = full ? p->s2 : p->s;
   la.rhs_stride = la.comp_stride * p->c;
   la.split = full ? 0 : 1;
-  leaf_tiling(la.N, la.c, nrhs, sizeof(T), la.rq, la.Lt);
+  leaf_tiling(la.N, la.c, nrhs, esz, la.rq, la.Lt);
+  if (rq > 0) la.rq = std::min(rq, std::max(1, nrhs));
+  if (Lt > 0) la.Lt = Lt;
+  while ((la.Lt > 1 || la.rq > 1) && leaf_smem_bytes(la.N, la.c, la.rq, la.Lt, esz) > 96 * 1024) {
+    if (la.Lt > 1) la.Lt /= 2; else la.rq = (la.rq + 1) / 2;
+  }
   const long long nlt = (la.lines + la.Lt - 1) / la.Lt;
   const long long nrc = (nrhs + la.rq - 1) / la.rq;
   la.tiles_per_node = nlt * nrc;
@@ -495,6 +473,13 @@ static btmv_status leaf_launch(btmv_plan p, int nrhs, int nn, const LeafNode* no
   for (int i = 0; i < nn; ++i) la.nodes[i] = nodes[i];
   la.fft = p->fft_apply[d - 1];
   la.sym = p->symdev;
+  return la;
+}
+
+template <class T>
+static btmv_status leaf_launch(btmv_plan p, int nrhs, int nn, const LeafNode* nodes, bool full,
+                               cudaStream_t st) {
+  LeafArgs la = leaf_step_args(p, nrhs, nn, nodes, full, sizeof(T), 0, 0);
   ProfScope ps(p, full ? BTMV_K_FULL_LEAF : BTMV_K_LEAF, st);
   cudaError_t e = (!(p->flags & BTMV_FLAG_GENERIC) && leaf_reg_supported(la, sizeof(T))) ? launch_leaf_reg(la, st)
                                                                                          : launch_leaf<T>(la, st);
@@ -504,39 +489,53 @@ static btmv_status leaf_launch(btmv_plan p, int nrhs, int nn, const LeafNode* no
 
 #define TRY(x) do { btmv_status s_ = (x); if (s_ != BTMV_OK) return s_; } while (0)
 
-// Depth-first traversal of Algorithm 1 (see btmv_apply in btmv.h).
-template <class T>
-static btmv_status split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, int nrhs, cudaStream_t st);
+// Depth-first traversal of Algorithm 1 (see btmv_apply in btmv.h): a node at
+// level m (transformed along dims 0..m-1) is split along dim m into itself
+// (even half) and W[m] (odd half); at the last split level both children go
+// to one leaf launch; merges run on the way back up.
+static void split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, std::vector<Step>& out);
 
-template <class T>
-static btmv_status split_descend(btmv_plan p, int m, void* buf, int prefix, int nrhs, cudaStream_t st) {
+static void split_descend(btmv_plan p, int m, void* buf, int prefix, std::vector<Step>& out) {
   void* Wm = p->W[m];
-  TRY(split_pass<T>(p, 0, m, nrhs, buf, nullptr, buf, Wm, st));
-  TRY(split_children<T>(p, m, buf, Wm, prefix, prefix | (1 << m), nrhs, st));
-  TRY(split_pass<T>(p, 1, m, nrhs, buf, Wm, buf, nullptr, st));
-  return BTMV_OK;
+  Step f = {0, m, buf, nullptr, buf, Wm, 0, {}};
+  out.push_back(f);
+  split_children(p, m, buf, Wm, prefix, prefix | (1 << m), out);
+  Step g = {1, m, buf, Wm, buf, nullptr, 0, {}};
+  out.push_back(g);
 }
 
-template <class T>
-static btmv_status split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, int nrhs, cudaStream_t st) {
+static void split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, std::vector<Step>& out) {
   if (m + 1 == p->d - 1) {
-    LeafNode nodes[2] = {{e, e, pe}, {o, o, po}};
-    return leaf_launch<T>(p, nrhs, 2, nodes, false, st);
+    Step l = {2, p->d - 1, nullptr, nullptr, nullptr, nullptr, 2, {{e, e, pe}, {o, o, po}}};
+    out.push_back(l);
+    return;
   }
-  TRY(split_descend<T>(p, m + 1, e, pe, nrhs, st));
-  TRY(split_descend<T>(p, m + 1, o, po, nrhs, st));
-  return BTMV_OK;
+  split_descend(p, m + 1, e, pe, out);
+  split_descend(p, m + 1, o, po, out);
+}
+
+void btmv::split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& out) {
+  out.clear();
+  if (p->d == 1) {
+    Step l = {2, 0, nullptr, nullptr, nullptr, nullptr, 1, {{x, y, 0}, {}}};
+    out.push_back(l);
+    return;
+  }
+  Step f = {0, 0, x, nullptr, y, p->W[0], 0, {}};
+  out.push_back(f);
+  split_children(p, 0, y, p->W[0], 0, 1, out);
+  Step g = {1, 0, y, p->W[0], y, nullptr, 0, {}};
+  out.push_back(g);
 }
 
 template <class T>
 static btmv_status split_apply(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
-  if (p->d == 1) {
-    LeafNode nd = {x, y, 0};
-    return leaf_launch<T>(p, nrhs, 1, &nd, false, st);
+  std::vector<Step> steps;
+  split_steps(p, x, y, steps);
+  for (const Step& s : steps) {
+    if (s.kind == 2) TRY(leaf_launch<T>(p, nrhs, s.nn, s.nodes, false, st));
+    else             TRY(split_pass<T>(p, s, nrhs, st));
   }
-  TRY(split_pass<T>(p, 0, 0, nrhs, x, nullptr, y, p->W[0], st));
-  TRY(split_children<T>(p, 0, y, p->W[0], 0, 1, nrhs, st));
-  TRY(split_pass<T>(p, 1, 0, nrhs, y, p->W[0], y, nullptr, st));
   return BTMV_OK;
 }
 
@@ -681,6 +680,7 @@ btmv_status btmv_apply_on_device(btmv_plan p, const void* x, void* y, int nrhs, 
   return apply_device(p, x, y, nrhs, st);
 }
 btmv_status btmv_set_error(btmv_status st, const char* msg) { return fail(st, "%s", msg); }
+int btmv_is_device_ptr(const void* ptr) { return is_device_ptr(ptr); }
 
 extern "C" btmv_status btmv_apply(btmv_plan p, const void* x, void* y, int nrhs, void* stream) {
   g_err.clear();
@@ -712,32 +712,11 @@ extern "C" btmv_status btmv_apply(btmv_plan p, const void* x, void* y, int nrhs,
   return BTMV_OK;
 }
 
-extern "C" btmv_status btmv_apply_batched(int count, const btmv_plan* plans, const void* const* x, void* const* y,
-                                          const int* nrhs, void* stream) {
-  g_err.clear();
-  if (count < 0) return fail(BTMV_E_ARG, "apply_batched: count < 0");
-  if (count == 0) return BTMV_OK;
-  if (!plans || !x || !y || !nrhs) return fail(BTMV_E_ARG, "apply_batched: NULL array");
-  for (int i = 0; i < count; ++i) {
-    TRY(check_apply(plans[i], x[i], y[i], nrhs[i]));
-    for (int j = 0; j < i; ++j)
-      if (plans[j] == plans[i]) return fail(BTMV_E_ARG, "apply_batched: plan %d repeated at %d", j, i);
-    if (nrhs[i] && (!is_device_ptr(x[i]) || !is_device_ptr(y[i])))
-      return fail(BTMV_E_ARG, "apply_batched: entry %d is not a device pointer", i);
-  }
-  cudaStream_t st = (cudaStream_t)stream;
-  for (int i = 0; i < count; ++i) {
-    if (!nrhs[i]) continue;
-    plans[i]->launches = 0;
-    TRY(apply_device(plans[i], x[i], y[i], nrhs[i], st));
-  }
-  return BTMV_OK;
-}
-
 extern "C" btmv_status btmv_destroy(btmv_plan p) {
   g_err.clear();
   if (!p) return BTMV_OK;
   cudaDeviceSynchronize();
+  batch_forget_plan(p);
   free_plan(p);
   return BTMV_OK;
 }

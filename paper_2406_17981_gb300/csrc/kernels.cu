@@ -87,7 +87,7 @@ __device__ __forceinline__ void pass_store(T* __restrict__ dst, const T* __restr
 }
 
 template <class T, int MODE, bool LF>
-__device__ __forceinline__ void pass_body(const PassArgs& a, unsigned char* smem) {
+__device__ __forceinline__ void pass_body(const PassArgs& a, unsigned char* smem, long long tile) {
   const PassGeom& g = a.g;
   const int TL = g.TL, N = g.N;
   const int ls = g.contig ? (N | 1) : 1;
@@ -100,7 +100,7 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, unsigned char* smem
   T* B2 = B1 + bufsz;
   const T* ph = (const T*)a.fft.ph;
 
-  const long long tile0 = (long long)blockIdx.x * TL;
+  const long long tile0 = tile * TL;
   for (int l = threadIdx.x; l < TL; l += blockDim.x) {
     const long long gl = tile0 + l;
     int ok = gl < g.lines;
@@ -157,8 +157,8 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, unsigned char* smem
 template <class T, int MODE>
 __global__ void __launch_bounds__(256) k_pass(const PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  if (a.g.contig) pass_body<T, MODE, false>(a, smem);
-  else            pass_body<T, MODE, true>(a, smem);
+  if (a.g.contig) pass_body<T, MODE, false>(a, smem, blockIdx.x);
+  else            pass_body<T, MODE, true>(a, smem, blockIdx.x);
 }
 
 static const size_t kMaxSmem = 227 * 1024;
@@ -231,8 +231,7 @@ __device__ __forceinline__ void leaf_multiply(T* __restrict__ R, const LeafArgs&
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_leaf(const LeafArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void leaf_body(const LeafArgs& a, unsigned char* smem, long long tile, int node) {
   const int N = a.N, c = a.c, rq = a.rq, Lt = a.Lt;
   const int NV = rq * c * Lt;
   const int ls = N | 1;
@@ -243,9 +242,8 @@ __global__ void __launch_bounds__(256) k_leaf(const LeafArgs a) {
   T* B1 = B0 + bufsz;
   const T* ph = (const T*)a.fft.ph;
 
-  const LeafNode nd = a.nodes[blockIdx.y];
+  const LeafNode nd = a.nodes[node];
   const long long nlt = (a.lines + Lt - 1) / Lt;
-  const long long tile = blockIdx.x;
   const long long lt = tile % nlt;
   const int q0 = (int)(tile / nlt) * rq;
   const long long l0 = lt * Lt;
@@ -311,6 +309,12 @@ __global__ void __launch_bounds__(256) k_leaf(const LeafArgs a) {
 }
 
 template <class T>
+__global__ void __launch_bounds__(256) k_leaf(const LeafArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  leaf_body<T>(a, smem, blockIdx.x, blockIdx.y);
+}
+
+template <class T>
 cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t st) {
   const size_t sm = leaf_smem_bytes(a.N, a.c, a.rq, a.Lt, sizeof(T));
   if (sm > kMaxSmem) return cudaErrorInvalidValue;
@@ -321,6 +325,113 @@ cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t st) {
   dim3 grid((unsigned)a.tiles_per_node, (unsigned)a.nnodes);
   k_leaf<T><<<grid, 256, sm, st>>>(a);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- persistent
+// One launch runs the line passes of many independent problems.  Items
+// (stage, tile) are handed out in increasing order by one atomic counter;
+// an item first waits until the stage it depends on has finished all its
+// tiles, so every wait is for items already taken by running blocks and the
+// launch cannot deadlock whatever the grid size.  Waits are bounded: past
+// the time or iteration limit the block records BTMV_E_TIMEOUT in the
+// control word, skips the tile, and later waits give up at once.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_persistent(const BatchStage* __restrict__ stages, int nstages,
+                                                    long long nitems, BatchCtl* ctl, unsigned* done,
+                                                    long long timeout_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long s_item;
+  __shared__ int s_stage, s_skip;
+  BatchStage* sst = (BatchStage*)smem;
+  unsigned char* work = smem + align_up(sizeof(BatchStage), 16);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long it = (long long)atomicAdd(&ctl->next, 1ULL);
+      s_item = it;
+      s_skip = 0;
+      if (it < nitems) {
+        int lo = 0, hi = nstages - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (stages[mid].item0 <= it) lo = mid; else hi = mid - 1;
+        }
+        s_stage = lo;
+        const int dep = stages[lo].dep;
+        if (dep >= 0) {
+          const unsigned need = (unsigned)stages[dep].tiles + (unsigned)ctl->withhold;
+          const unsigned long long t0 = global_ns();
+          long long iter = 0;
+          while (*(volatile unsigned*)&done[dep] < need) {
+            if (*(volatile int*)&ctl->error) { s_skip = 1; break; }
+            if (++iter > 200000000LL || (long long)(global_ns() - t0) > timeout_ns) {
+              atomicCAS(&ctl->error, 0, (int)BTMV_E_TIMEOUT);
+              ctl->err_stage = lo;
+              s_skip = 1;
+              break;
+            }
+            __nanosleep(256);
+          }
+        }
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    const long long it = s_item;
+    if (it >= nitems) break;
+    const int si = s_stage;
+    if (!s_skip) {
+      const int* src = (const int*)&stages[si];
+      int* dst = (int*)sst;
+      for (int i = threadIdx.x; i < (int)(sizeof(BatchStage) / 4); i += blockDim.x) dst[i] = src[i];
+      __syncthreads();
+      const long long tile = it - sst->item0;
+      if (sst->kind == 2) {
+        leaf_body<T>(sst->la, work, tile % sst->la.tiles_per_node, (int)(tile / sst->la.tiles_per_node));
+      } else if (sst->kind == 0) {
+        if (sst->pa.g.contig) pass_body<T, 0, false>(sst->pa, work, tile);
+        else                  pass_body<T, 0, true>(sst->pa, work, tile);
+      } else if (sst->kind == 1) {
+        if (sst->pa.g.contig) pass_body<T, 1, false>(sst->pa, work, tile);
+        else                  pass_body<T, 1, true>(sst->pa, work, tile);
+      }                        // kind 3: no work (self test)
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&done[si], 1u);
+    }
+  }
+}
+
+template <class T>
+cudaError_t launch_persistent(const BatchStage* stages, int nstages, long long nitems, BatchCtl* ctl,
+                              unsigned* done, long long timeout_ns, int grid, size_t smem, cudaStream_t st) {
+  // the kernel also holds a few bytes of static shared memory
+  const size_t dyn_max = kMaxSmem - 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (smem + align_up(sizeof(BatchStage), 16) > dyn_max) return cudaErrorInvalidValue;
+  k_persistent<T><<<grid, 256, smem + align_up(sizeof(BatchStage), 16), st>>>(stages, nstages, nitems, ctl, done,
+                                                                            timeout_ns);
+  return cudaGetLastError();
+}
+
+template <class T>
+int persistent_blocks_per_sm(size_t smem) {
+  int nb = 0;
+  cudaFuncSetAttribute(k_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSmem - 1024));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<T>, 256, smem + align_up(sizeof(BatchStage), 16));
+  return nb;
 }
 
 // ----------------------------------------------------------------- symbol
@@ -405,5 +516,11 @@ template cudaError_t launch_pass<float2>(int, const PassArgs&, cudaStream_t);
 template cudaError_t launch_pass<double2>(int, const PassArgs&, cudaStream_t);
 template cudaError_t launch_leaf<float2>(const LeafArgs&, cudaStream_t);
 template cudaError_t launch_leaf<double2>(const LeafArgs&, cudaStream_t);
+template cudaError_t launch_persistent<float2>(const BatchStage*, int, long long, BatchCtl*, unsigned*, long long, int,
+                                               size_t, cudaStream_t);
+template cudaError_t launch_persistent<double2>(const BatchStage*, int, long long, BatchCtl*, unsigned*, long long,
+                                                int, size_t, cudaStream_t);
+template int persistent_blocks_per_sm<float2>(size_t);
+template int persistent_blocks_per_sm<double2>(size_t);
 
 }  // namespace btmv

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/btmv.h"
 #include "fft.cuh"
 
 namespace btmv {
@@ -107,10 +108,32 @@ struct StoreArgs {
   long long blk;
 };
 
+// A stage of the batched persistent launch: one line pass or leaf launch of
+// one problem, with the stage it waits for.
+struct BatchStage {
+  int kind;            // 0 forward split pass, 1 merge pass, 2 leaf, 3 no work
+  int dep;             // stage index this one waits for, -1 for none
+  long long item0;     // first work item of this stage
+  long long tiles;     // work items (tiles) of this stage
+  PassArgs pa;
+  LeafArgs la;
+};
+struct BatchCtl {
+  unsigned long long next;   // work-item dispenser
+  int error;                 // 0, or BTMV_E_TIMEOUT when a wait expired
+  int err_stage;             // stage whose wait expired
+  int withhold;              // self test: completion count a wait never reaches
+  int pad;
+};
+
 // launchers (return cudaGetLastError())
 template <class T> cudaError_t launch_pass(int mode, const PassArgs& a, cudaStream_t st);
 template <class T> cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t st);
 cudaError_t launch_fold(const FoldArgs& a, cudaStream_t st);
+template <class T>
+cudaError_t launch_persistent(const BatchStage* stages, int nstages, long long nitems, BatchCtl* ctl, unsigned* done,
+                              long long timeout_ns, int grid, size_t smem, cudaStream_t st);
+template <class T> int persistent_blocks_per_sm(size_t smem);
 cudaError_t launch_store(const StoreArgs& a, cudaStream_t st);
 
 // register-resident kernels for power-of-two lines (complex64); the

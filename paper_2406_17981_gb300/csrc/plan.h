@@ -1,0 +1,84 @@
+// Internal plan representation and schedule helpers of libbtmv (shared by
+// the per-call launcher, btmv.cu, and the batched persistent launcher,
+// batch.cu).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <vector>
+
+#include "../../include/btmv.h"
+#include "kernels.cuh"
+
+namespace btmv {
+
+struct TableSet {
+  void* mem = nullptr;                 // device
+  std::map<int, size_t> off_f, off_d;  // N -> byte offset of [tw N][ph N]
+  size_t bytes = 0;
+};
+
+}  // namespace btmv
+
+// The opaque plan of the C ABI (global namespace, as declared in btmv.h).
+struct btmv_plan_s {
+  int d = 0, c = 0, prec = 0, algo = 0, max_rhs = 0;
+  uint32_t flags = 0;
+  int n[btmv::MAX_D] = {1, 1, 1, 1};
+  long long s = 1;          // prod n
+  long long s2 = 1;         // prod 2n
+  size_t esz = 8;           // bytes per complex
+  int dev = 0;
+  btmv::TableSet tab;
+  btmv::FftDev fft_apply[btmv::MAX_D];  // per dim, plan precision (N = n_m split, 2 n_m full)
+  btmv::FftDev fft_sym[btmv::MAX_D];    // per dim, FP64, N = n_m
+  // symbol
+  void* sym = nullptr;
+  size_t sym_bytes = 0;
+  btmv::SymDev symdev;
+  bool has_sym = false;
+  int nsym = 0;
+  int compressed = 0;
+  // workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  std::vector<void*> W;     // split: d-1 vectors; full: Z
+  // host staging
+  void* stage_x = nullptr;
+  void* stage_y = nullptr;
+  // profiling
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  double acc_ms[BTMV_K_NKINDS] = {0};
+  int64_t acc_n[BTMV_K_NKINDS] = {0};
+  int launches = 0;
+};
+
+namespace btmv {
+
+// One launch of the depth-first schedule of Algorithm 1.
+struct Step {
+  int kind;            // 0 forward split pass, 1 merge pass, 2 leaf
+  int dim;             // level (dimension) of a pass
+  const void* in0;
+  const void* in1;
+  void* out0;
+  void* out1;
+  int nn;              // leaf: number of nodes
+  LeafNode nodes[2];
+};
+
+btmv_status fail(btmv_status st, const char* fmt, ...);
+// Radix factorisation of N into stages: mode 0 prefers radix 16, mode 1 radix 8.
+bool factor_radices_mode(int N, FftDev& f, int mode);
+// Steps of one split apply on device pointers (d >= 1).
+void split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& out);
+// Arguments of a split pass step; TL = 0 picks the default tile.
+PassArgs split_pass_args(btmv_plan p, const Step& s, int nrhs, size_t esz, int TL);
+// Arguments of a leaf step; Lt, rq = 0 pick the defaults.
+LeafArgs leaf_step_args(btmv_plan p, int nrhs, int nn, const LeafNode* nodes, bool full, size_t esz, int Lt, int rq);
+// Drop every cached batch that refers to plan p (called by btmv_destroy).
+void batch_forget_plan(btmv_plan p);
+
+}  // namespace btmv
