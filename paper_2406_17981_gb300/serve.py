@@ -1,0 +1,246 @@
+"""Continuous-batching matvec server for concurrent iterative solves.
+
+Many solves (BiCGSTAB on A = I - alpha T, T a block Toeplitz operator) run at
+once.  Each admitted solve keeps its plan (symbol, twiddles, workspace) and
+its Krylov vectors resident on the GPU; solves are admitted in arrival order
+while their device footprint fits an HBM budget, and leave (freeing their
+memory) when they finish.  Every scheduler tick gathers the matvec requests
+of all solves that are ready and runs them as ONE btmv_apply_batched launch
+(one persistent kernel across all of them); while a batch is on the GPU the
+host admits newcomers, runs the Krylov updates of finished requests and forms
+the next batch, with up to ``max_inflight`` batches queued on the device.
+
+The matvec is the library's (C ABI); the Krylov updates are plain torch
+vector operations on the device.  Latency of a request = time from the moment
+its input is ready to the moment its result is visible to the host.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import os
+import time
+
+import numpy as np
+
+from . import analysis as A
+from . import btmv as bt
+
+
+class SolveSpec:
+    """One solve: grid n (d = len(n)), c components, generator (t, parity,
+    flags), right-hand side seed, alpha scaling of A = I - alpha T, and the
+    matvec budget."""
+
+    def __init__(self, n, c, t, parity, sym_flags, alpha, b_seed, max_matvecs=60, tol=1e-6, arrival=0.0,
+                 name=""):
+        self.n = tuple(int(v) for v in n)
+        self.c = int(c)
+        self.t, self.parity, self.sym_flags = t, parity, sym_flags
+        self.alpha = float(alpha)
+        self.b_seed = int(b_seed)
+        self.max_matvecs = int(max_matvecs)
+        self.tol = float(tol)
+        self.arrival = float(arrival)
+        self.name = name
+
+    def footprint(self, nvec=9) -> int:
+        """Device bytes of an admitted solve: symbol, workspace, twiddles and
+        nvec vectors (matvec input/output plus the BiCGSTAB vectors)."""
+        d = len(self.n)
+        V = A.vector_bytes(self.n, self.c, 1, 8)
+        compressed = bool(self.sym_flags & bt.BTMV_SYM_PARITY)
+        sym = A.symbol_bytes(self.n, self.c, 8, bool(self.sym_flags & bt.BTMV_SYM_BLOCK), compressed)
+        return sym + (d - 1) * V + nvec * V + 64 * 1024
+
+
+class Solve:
+    """BiCGSTAB state machine; each call of ``step`` consumes the last matvec
+    result and returns True when it has put a new request in ``self.xin``."""
+
+    def __init__(self, spec: SolveSpec, plan, torch, algo):
+        self.spec = spec
+        self.plan = plan
+        self.torch = torch
+        shape = (1, spec.c) + spec.n
+        dev = "cuda"
+        g = np.random.default_rng(spec.b_seed)
+        b = (g.standard_normal(shape) + 1j * g.standard_normal(shape)).astype(np.complex64)
+        self.b = torch.from_numpy(b).to(dev)
+        z = lambda: torch.zeros(shape, dtype=torch.complex64, device=dev)  # noqa: E731
+        self.xin, self.yout = z(), z()
+        self.x = z()
+        self.r = self.b.clone()
+        self.r0 = self.b.clone()
+        self.p, self.v, self.s, self.tv = z(), z(), z(), z()
+        self.rho = self.alpha_k = self.omega = 1.0 + 0j
+        self.bnorm = float(torch.linalg.vector_norm(self.b))
+        self.phase = "start"
+        self.matvecs = 0
+        self.done = False
+        self.resid = 1.0
+        self.history = []
+        self.algo = algo
+
+    # A w = w - alpha T w, with T w the last matvec result
+    def _apply_A(self, w, tw):
+        return w - self.spec.alpha * tw
+
+    def step(self) -> bool:
+        th = self.torch
+        if self.phase == "start":
+            self.rho = complex(th.vdot(self.r0.flatten(), self.r.flatten()))
+            self.p.copy_(self.r)
+            self.xin.copy_(self.p)
+            self.phase = "v"
+            return True
+        if self.phase == "v":                      # yout = T p
+            self.v = self._apply_A(self.p, self.yout)
+            den = complex(th.vdot(self.r0.flatten(), self.v.flatten()))
+            self.alpha_k = self.rho / den if den != 0 else 0.0
+            self.s = self.r - self.alpha_k * self.v
+            if float(th.linalg.vector_norm(self.s)) <= self.spec.tol * self.bnorm:
+                self.x += self.alpha_k * self.p
+                return self._finish(float(th.linalg.vector_norm(self.s)))
+            self.xin.copy_(self.s)
+            self.phase = "t"
+            return True
+        if self.phase == "t":                      # yout = T s
+            self.tv = self._apply_A(self.s, self.yout)
+            tt = float(th.vdot(self.tv.flatten(), self.tv.flatten()).real)
+            self.omega = complex(th.vdot(self.tv.flatten(), self.s.flatten())) / tt if tt > 0 else 0.0
+            self.x += self.alpha_k * self.p + self.omega * self.s
+            self.r = self.s - self.omega * self.tv
+            res = float(th.linalg.vector_norm(self.r)) / self.bnorm
+            self.history.append(res)
+            if res <= self.spec.tol or self.matvecs + 2 > self.spec.max_matvecs:
+                return self._finish(res * self.bnorm)
+            rho_new = complex(th.vdot(self.r0.flatten(), self.r.flatten()))
+            beta = (rho_new / self.rho) * (self.alpha_k / self.omega) if self.rho != 0 and self.omega != 0 else 0.0
+            self.rho = rho_new
+            self.p = self.r + beta * (self.p - self.omega * self.v)
+            self.xin.copy_(self.p)
+            self.phase = "v"
+            return True
+        return False
+
+    def _finish(self, rnorm):
+        self.resid = rnorm / self.bnorm
+        self.done = True
+        return False
+
+
+class Server:
+    """Continuous-batching server.  ``run(specs)`` plays the arrivals in
+    ``spec.arrival`` (seconds after start) and returns statistics."""
+
+    def __init__(self, budget_bytes=80 * 10 ** 9, max_inflight=2, algo=bt.BTMV_ALGO_SPLIT, batched=True,
+                 record=None):
+        import torch
+        self.torch = torch
+        self.budget = int(budget_bytes)
+        self.max_inflight = max(1, int(max_inflight))
+        self.algo = algo
+        self.batched = batched
+        self.record = record          # optional: {solve name: [(x, y), ...]} filled with matvec pairs
+        self.streams = [torch.cuda.Stream() for _ in range(self.max_inflight)]
+
+    def _admit(self, spec):
+        p = bt.Plan(spec.n, spec.c, bt.BTMV_C64, self.algo, max_rhs=1)
+        p.set_kernel(spec.t, spec.sym_flags, spec.parity)
+        return Solve(spec, p, self.torch, self.algo)
+
+    def run(self, specs):
+        th = self.torch
+        if self.batched:
+            os.environ.setdefault("BTMV_NO_AUTOTUNE", "1")     # request mixes change every tick
+        pending = collections.deque(sorted(specs, key=lambda s: s.arrival))
+        active, ready = [], []
+        inflight = collections.deque()                       # (event, [solves], t_launch)
+        used = 0
+        lat, t_ready = [], {}
+        peak_active = 0
+        nbatches = 0
+        batch_sizes = []
+        matvecs = 0
+        t0 = time.perf_counter()
+        finished = []
+        while pending or active or inflight:
+            now = time.perf_counter() - t0
+            # admission by arrival time and HBM budget
+            while pending and pending[0].arrival <= now and used + pending[0].footprint() <= self.budget:
+                spec = pending.popleft()
+                s = self._admit(spec)
+                used += spec.footprint()
+                s.step()                                     # first request
+                active.append(s)
+                ready.append(s)
+                t_ready[id(s)] = time.perf_counter()
+            if pending and not active and not inflight and pending[0].footprint() > self.budget:
+                raise RuntimeError(f"solve {pending[0].name} does not fit the HBM budget")
+            peak_active = max(peak_active, len(active))
+            # completions
+            while inflight and (inflight[0][0].query() or len(inflight) >= self.max_inflight and not ready):
+                ev, batch, _ = inflight.popleft()
+                ev.synchronize()
+                tdone = time.perf_counter()
+                for s in batch:
+                    lat.append(tdone - t_ready.pop(id(s)))
+                    s.matvecs += 1
+                    if self.record is not None and s.spec.name in self.record:
+                        self.record[s.spec.name].append((s.xin.clone(), s.yout.clone()))
+                    if s.step():
+                        ready.append(s)
+                        t_ready[id(s)] = time.perf_counter()
+                    elif s.done:
+                        active.remove(s)
+                        used -= s.spec.footprint()
+                        finished.append(s)
+            # launch the ready requests as one batch
+            if ready and len(inflight) < self.max_inflight:
+                batch, ready = ready, []
+                st = self.streams[nbatches % self.max_inflight]
+                st.wait_stream(th.cuda.current_stream())     # Krylov updates done
+                if self.batched:
+                    bt.btmv_apply_batched([s.plan.handle for s in batch], [s.xin for s in batch],
+                                          [s.yout for s in batch], [1] * len(batch), stream=st)
+                else:
+                    for s in batch:
+                        bt.btmv_apply(s.plan.handle, s.xin, s.yout, 1, stream=st)
+                ev = th.cuda.Event()
+                ev.record(st)
+                th.cuda.current_stream().wait_event(ev)
+                inflight.append((ev, batch, time.perf_counter()))
+                nbatches += 1
+                batch_sizes.append(len(batch))
+                matvecs += len(batch)
+            elif not ready and not inflight and pending:
+                time.sleep(max(0.0, min(0.001, pending[0].arrival - (time.perf_counter() - t0))))
+        th.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        for s in finished:
+            s.plan.close()
+        lat_ms = np.array(lat) * 1e3
+        return {
+            "matvecs": matvecs, "wall_s": wall, "matvecs_per_s": matvecs / wall,
+            "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
+            "batches": nbatches, "mean_batch": float(np.mean(batch_sizes)) if batch_sizes else 0.0,
+            "peak_active_solves": peak_active, "solves": len(finished),
+            "max_residual": max((s.resid for s in finished), default=0.0),
+            "solutions": {s.spec.name: s.x for s in finished},
+        }
+
+
+def scaled_alpha(spec_t, parity, sym_flags, n, c):
+    """alpha = 0.5 / max over frequencies of |symbol| (spectral norm bound of
+    the scalar or per-block maximum), so that ||alpha T|| <= 1/2 and
+    BiCGSTAB on I - alpha T converges quickly.  Computed from the library's
+    own symbol (full 2n-grid transform scaled back to the unnormalised
+    coefficients)."""
+    p = bt.Plan(n, c, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT)
+    p.set_kernel(spec_t, sym_flags, parity)
+    S = bt.btmv_get_symbol(p.handle)
+    p.close()
+    scale = float(np.prod([2 * m for m in n]))
+    return 0.5 / (c * float(np.abs(S).max()) * scale)

@@ -1,0 +1,89 @@
+"""Continuous-batching server: concurrent BiCGSTAB solves share batched
+matvec launches; each result must be the same alone and in the mix."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import embed as OE
+from tests.gpu_util import rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+bt = pytest.importorskip("paper_2406_17981_gb300.btmv")
+serve = pytest.importorskip("paper_2406_17981_gb300.serve")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    bt.lib()
+
+
+def make_specs(shapes, arrival_gap=0.002):
+    specs = []
+    for k, (n, c) in enumerate(shapes):
+        if c == 3:
+            t, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+        else:
+            t, par = W.green_scalar_orthant(n, kh=W.KH_GREEN)
+        flags = (bt.BTMV_SYM_BLOCK if c == 3 else 0) | bt.BTMV_SYM_PARITY
+        alpha = serve.scaled_alpha(t, par, flags, n, c)
+        specs.append(serve.SolveSpec(n, c, t, par, flags, alpha, b_seed=100 + k, max_matvecs=40, tol=1e-5,
+                                     arrival=k * arrival_gap, name=f"s{k}"))
+    return specs
+
+
+SHAPES = [((32, 32), 1), ((12, 16, 10), 3), ((48, 32), 1), ((16, 16, 16), 3), ((24, 20), 1),
+          ((8, 12, 24), 3), ((64, 48), 1), ((20, 20, 12), 3)]
+
+
+def test_solves_alone_and_in_the_mix_agree():
+    specs = make_specs(SHAPES)
+    record = {"s1": [], "s2": []}
+    mix = serve.Server(budget_bytes=8 * 10 ** 9, record=record).run(specs)
+    assert mix["solves"] == len(specs)
+    assert mix["mean_batch"] > 1.0                 # requests really were batched together
+    assert mix["max_residual"] <= 1e-4
+    for spec in specs:
+        alone = serve.Server(budget_bytes=8 * 10 ** 9).run([serve.SolveSpec(
+            spec.n, spec.c, spec.t, spec.parity, spec.sym_flags, spec.alpha, spec.b_seed,
+            spec.max_matvecs, spec.tol, 0.0, spec.name)])
+        a = alone["solutions"][spec.name].cpu().numpy().astype(np.complex128)
+        m = mix["solutions"][spec.name].cpu().numpy().astype(np.complex128)
+        assert rel(m, a) <= 1e-4, spec.name
+    # every recorded matvec of the mix equals the same matvec done alone
+    for name, pairs in record.items():
+        spec = specs[int(name[1:])]
+        p = bt.Plan(spec.n, spec.c, bt.BTMV_C64)
+        p.set_kernel(spec.t, spec.sym_flags, spec.parity)
+        for x, y in pairs:
+            ya = torch.zeros_like(y)
+            p.apply(x, ya, 1)
+            torch.cuda.synchronize()
+            assert rel(y.cpu().numpy().astype(np.complex128), ya.cpu().numpy().astype(np.complex128)) <= 1e-5
+        p.close()
+
+
+def test_solution_solves_the_system_by_the_oracle():
+    specs = make_specs([((12, 16, 10), 3)])
+    out = serve.Server().run(specs)
+    spec = specs[0]
+    x = out["solutions"][spec.name].cpu().numpy().astype(np.complex128)[0]
+    g = np.random.default_rng(spec.b_seed)
+    shape = (1, spec.c) + spec.n
+    b = (g.standard_normal(shape) + 1j * g.standard_normal(shape)).astype(np.complex64)[0].astype(np.complex128)
+    Tx = OE.embed_matvec(W.orthant_to_full(spec.t, spec.parity), x)
+    assert rel(x - spec.alpha * Tx, b) <= 1e-4
+
+
+def test_admission_respects_the_hbm_budget():
+    specs = make_specs([((16, 16, 16), 3)] * 4, arrival_gap=0.0)
+    budget = specs[0].footprint() * 2 + 1            # room for two solves at a time
+    out = serve.Server(budget_bytes=budget).run(specs)
+    assert out["solves"] == 4
+    assert out["peak_active_solves"] <= 2
