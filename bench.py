@@ -460,7 +460,7 @@ def run_batched(args):
 def serving_specs(count=200, seed=7):
     """Config: 200 solves, half d=2 c=1 scalar Green on 256^2..1024^2, half
     d=3 c=3 dyadic Green on 32^3..192^3 (7-smooth sizes), BiCGSTAB on
-    I - alpha T with ||alpha T|| <= 1/2, <= 60 matvecs each, Poisson arrivals
+    I - alpha T with ||alpha T|| <= 0.9, tolerance 1e-6, <= 60 matvecs each, Poisson arrivals
     (mean gap 5 ms) so that nearly all solves are in flight together."""
     from paper_2406_17981_gb300 import btmv as bt
     from paper_2406_17981_gb300 import serve
@@ -482,10 +482,10 @@ def serving_specs(count=200, seed=7):
         t, par = gens[n]
         flags = (bt.BTMV_SYM_BLOCK if c == 3 else 0) | bt.BTMV_SYM_PARITY
         if n not in alphas:
-            alphas[n] = serve.scaled_alpha(t, par, flags, n, c)
+            alphas[n] = serve.scaled_alpha(t, par, flags, n, c, target=0.9)
         tarr += float(rng.exponential(0.005))
         specs.append(serve.SolveSpec(n, c, t, par, flags, alphas[n], b_seed=1000 + k, max_matvecs=60,
-                                     tol=1e-5, arrival=tarr, name=f"solve{k}"))
+                                     tol=1e-6, arrival=tarr, name=f"solve{k}"))
     return specs
 
 

@@ -109,6 +109,20 @@ BTMV_API btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n, i
                              int precision, int algo, int max_rhs, uint32_t flags);
 
 /*
+ * btmv_plan_clone -- a new plan for the same operator: same geometry,
+ * precision and algorithm, sharing src's symbol store and twiddle tables
+ * (reference counted: they live until the last plan using them is
+ * destroyed) with its own workspace for up to max_rhs right-hand sides.
+ * Lets many concurrent solves of one operator keep a single resident symbol
+ * while each runs its own applies (one stream per plan).  A later
+ * btmv_set_kernel on any of them builds a private symbol for that plan only.
+ *   src      plan to clone (its symbol may or may not be set yet).
+ *   max_rhs  >= 1.   flags  BTMV_FLAG_*.   out  receives the new plan.
+ * Errors: BTMV_E_ARG, BTMV_E_NOMEM.
+ */
+BTMV_API btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flags, btmv_plan* out);
+
+/*
  * btmv_set_kernel -- set the generating coefficients (one-time symbol build).
  *   t         host, complex128 interleaved (2 doubles per value):
  *             without BTMV_SYM_PARITY: [c][c][2n_1 - 1]...[2n_d - 1], offset p_m

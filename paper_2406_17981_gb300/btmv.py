@@ -54,6 +54,7 @@ def lib() -> ctypes.CDLL:
         L = ctypes.CDLL(LIB_PATH)
         vp, i32, u32, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_int
         L.btmv_plan_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(ctypes.c_int32), i32, i32, i32, i32, u32]
+        L.btmv_plan_clone.argtypes = [vp, i32, u32, ctypes.POINTER(vp)]
         L.btmv_set_kernel.argtypes = [vp, ctypes.POINTER(ctypes.c_double), u32, ctypes.POINTER(ctypes.c_int8), vp]
         L.btmv_apply.argtypes = [vp, vp, vp, i32, vp]
         L.btmv_apply_host_noalloc.argtypes = [vp, vp, vp, i32, vp]
@@ -68,7 +69,7 @@ def lib() -> ctypes.CDLL:
         L.btmv_batch_tuning.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.btmv_selftest_wait_timeout.argtypes = [i32, vp]
-        for name in ("btmv_plan_create", "btmv_set_kernel", "btmv_apply", "btmv_apply_host_noalloc",
+        for name in ("btmv_plan_create", "btmv_plan_clone", "btmv_set_kernel", "btmv_apply", "btmv_apply_host_noalloc",
                      "btmv_apply_batched", "btmv_batch_tuning", "btmv_selftest_wait_timeout",
                      "btmv_destroy", "btmv_plan_get_info", "btmv_get_symbol", "btmv_profile_read"):
             getattr(L, name).restype = st
@@ -113,6 +114,12 @@ def btmv_plan_create(d, n, c, precision=BTMV_C64, algo=BTMV_ALGO_SPLIT, max_rhs=
     h = ctypes.c_void_p()
     _check(lib().btmv_plan_create(ctypes.byref(h), int(d), arr, int(c), int(precision), int(algo),
                                   int(max_rhs), int(flags)))
+    return h.value
+
+
+def btmv_plan_clone(plan, max_rhs=1, flags=0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().btmv_plan_clone(plan, int(max_rhs), int(flags), ctypes.byref(h)))
     return h.value
 
 
@@ -193,13 +200,18 @@ def btmv_profile_read(plan):
 class Plan:
     """Owning wrapper: ``Plan(n, c, ...)``; ``set_kernel``, ``apply``, ``close``."""
 
-    def __init__(self, n, c, precision=BTMV_C64, algo=BTMV_ALGO_SPLIT, max_rhs=1, flags=0):
+    def __init__(self, n, c, precision=BTMV_C64, algo=BTMV_ALGO_SPLIT, max_rhs=1, flags=0, _handle=None):
         self.n = tuple(int(v) for v in n)
         self.d = len(self.n)
         self.c = int(c)
         self.precision = precision
         self.max_rhs = int(max_rhs)
-        self.handle = btmv_plan_create(self.d, self.n, self.c, precision, algo, max_rhs, flags)
+        self.handle = _handle if _handle is not None else btmv_plan_create(self.d, self.n, self.c, precision,
+                                                                           algo, max_rhs, flags)
+
+    def clone(self, max_rhs=1, flags=0) -> "Plan":
+        """A plan sharing this plan's symbol and tables, with its own workspace."""
+        return Plan(self.n, self.c, self.precision, max_rhs=max_rhs, _handle=btmv_plan_clone(self.handle, max_rhs, flags))
 
     @property
     def info(self) -> dict:

@@ -107,6 +107,7 @@ static btmv_status build_tables(btmv_plan p, const std::vector<int>& Nf, const s
     for (int k = 0; k < N; ++k) { t[k] = make_double2((double)a[k], (double)b[k]); t[N + k] = make_double2((double)c[k], (double)d[k]); }
   }
   CUDA_TRY(cudaMalloc(&p->tab.mem, off));
+  p->tab.owner = std::make_shared<DevBuf>(p->tab.mem);
   CUDA_TRY(cudaMemcpy(p->tab.mem, host.data(), off, cudaMemcpyHostToDevice));
   return BTMV_OK;
 }
@@ -123,8 +124,8 @@ static void free_plan(btmv_plan p) {
   if (!p) return;
   for (auto& r : p->pending) { p->pool.push_back(r.a); p->pool.push_back(r.b); }
   for (auto e : p->pool) cudaEventDestroy(e);
-  if (p->tab.mem) cudaFree(p->tab.mem);
-  if (p->sym) cudaFree(p->sym);
+  p->tab.owner.reset();       // freed with the last plan sharing them
+  p->sym_owner.reset();
   if (p->ws) cudaFree(p->ws);
   if (p->stage_x) cudaFree(p->stage_x);
   if (p->stage_y) cudaFree(p->stage_y);
@@ -177,6 +178,35 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
     cudaError_t e = cudaMalloc(&p->ws, p->ws_bytes);
     if (e != cudaSuccess) { free_plan(p); return fail(BTMV_E_NOMEM, "plan_create: workspace of %zu bytes: %s", p->ws_bytes, cudaGetErrorString(e)); }
     if (algo == BTMV_ALGO_SPLIT)
+      for (size_t i = 0; i < nvec; ++i) p->W.push_back((unsigned char*)p->ws + i * V);
+    else
+      p->W.push_back(p->ws);
+  }
+  *out = p;
+  return BTMV_OK;
+}
+
+extern "C" btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flags, btmv_plan* out) {
+  g_err.clear();
+  if (!src || !out) return fail(BTMV_E_ARG, "plan_clone: NULL argument");
+  *out = nullptr;
+  if (max_rhs < 1) return fail(BTMV_E_ARG, "plan_clone: max_rhs=%d < 1", max_rhs);
+  if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC)) return fail(BTMV_E_ARG, "plan_clone: unknown flags 0x%x", flags);
+  btmv_plan p = new btmv_plan_s();
+  p->d = src->d; p->c = src->c; p->prec = src->prec; p->algo = src->algo; p->max_rhs = max_rhs; p->flags = flags;
+  for (int m = 0; m < MAX_D; ++m) { p->n[m] = src->n[m]; p->fft_apply[m] = src->fft_apply[m]; p->fft_sym[m] = src->fft_sym[m]; }
+  p->s = src->s; p->s2 = src->s2; p->esz = src->esz; p->dev = src->dev;
+  p->tab = src->tab;                                  // shared twiddle tables
+  p->sym = src->sym; p->sym_owner = src->sym_owner;   // shared symbol store
+  p->sym_bytes = src->sym_bytes; p->symdev = src->symdev; p->has_sym = src->has_sym;
+  p->nsym = src->nsym; p->compressed = src->compressed;
+  const size_t V = (size_t)max_rhs * p->c * p->s * p->esz;
+  const size_t nvec = p->algo == BTMV_ALGO_SPLIT ? (size_t)(p->d - 1) : 0;
+  p->ws_bytes = p->algo == BTMV_ALGO_SPLIT ? nvec * V : (size_t)max_rhs * p->c * p->s2 * p->esz;
+  if (p->ws_bytes) {
+    cudaError_t e = cudaMalloc(&p->ws, p->ws_bytes);
+    if (e != cudaSuccess) { free_plan(p); return fail(BTMV_E_NOMEM, "plan_clone: workspace of %zu bytes: %s", p->ws_bytes, cudaGetErrorString(e)); }
+    if (p->algo == BTMV_ALGO_SPLIT)
       for (size_t i = 0; i < nvec; ++i) p->W.push_back((unsigned char*)p->ws + i * V);
     else
       p->W.push_back(p->ws);
@@ -264,8 +294,9 @@ extern "C" btmv_status btmv_set_kernel(btmv_plan p, const double* t, uint32_t sy
   const size_t t_bytes = (size_t)c * c * tb * sizeof(double2);
   void* t_dev = nullptr;
   void* F = nullptr;
-  void* store = p->sym;
-  if (p->sym && p->sym_bytes != store_bytes) { cudaFree(p->sym); p->sym = nullptr; store = nullptr; p->has_sym = false; }
+  // reuse this plan's own store when it has the right size; a store shared
+  // with clones is left to them and a new one is built
+  void* store = (p->sym && p->sym_bytes == store_bytes && p->sym_owner.use_count() == 1) ? p->sym : nullptr;
   cudaError_t e = cudaMalloc(&t_dev, t_bytes);
   if (e != cudaSuccess) return fail(BTMV_E_NOMEM, "set_kernel: %zu bytes for t: %s", t_bytes, cudaGetErrorString(e));
   e = cudaMalloc(&F, (size_t)nsym * p->s * sizeof(double2));
@@ -335,7 +366,10 @@ extern "C" btmv_status btmv_set_kernel(btmv_plan p, const double* t, uint32_t sy
     if (store != p->sym) cudaFree(store);
     return ret;
   }
-  p->sym = store;
+  if (store != p->sym) {
+    p->sym_owner = std::make_shared<DevBuf>(store);
+    p->sym = store;
+  }
   p->sym_bytes = store_bytes;
   sd.data = store;
   p->symdev = sd;
@@ -393,10 +427,14 @@ static ArrMap contig_map(long long N, long long inner) {
   return am;
 }
 
+// Tile of lines for the generic pass: as many lines as fit 64 KB of shared
+// memory (at most 16 strided / 2048 points contiguous), then fewer while the
+// launch would have fewer than two blocks per SM.
 static void choose_tile(PassGeom& g, size_t esz) {
   int TL = g.contig ? std::max(1, std::min(64, 2048 / g.N)) : 16;
   g.TL = TL;
   while (TL > 1 && pass_smem_bytes(g, esz) > 64 * 1024) { TL /= 2; g.TL = TL; }
+  while (TL > 1 && (g.lines + TL - 1) / TL < 2 * 152) { TL /= 2; g.TL = TL; }
 }
 
 // Register-resident kernels where the geometry allows, else the generic
@@ -461,6 +499,8 @@ LeafArgs btmv::leaf_step_args(btmv_plan p, int nrhs, int nn, const LeafNode* nod
   la.rhs_stride = la.comp_stride * p->c;
   la.split = full ? 0 : 1;
   leaf_tiling(la.N, la.c, nrhs, esz, la.rq, la.Lt);
+  // enough blocks for small problems: at least two per SM over the nodes
+  while (la.Lt > 1 && ((la.lines + la.Lt - 1) / la.Lt) * nrhs * nn < 2 * 152) la.Lt /= 2;
   if (rq > 0) la.rq = std::min(rq, std::max(1, nrhs));
   if (Lt > 0) la.Lt = Lt;
   while ((la.Lt > 1 || la.rq > 1) && leaf_smem_bytes(la.N, la.c, la.rq, la.Lt, esz) > 96 * 1024) {

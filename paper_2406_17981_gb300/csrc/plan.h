@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <memory>
 #include <vector>
 
 #include "../../include/btmv.h"
@@ -12,8 +13,17 @@
 
 namespace btmv {
 
+// Device allocation shared by reference count (twiddle tables and symbol
+// stores are shared between a plan and its clones).
+struct DevBuf {
+  void* ptr = nullptr;
+  explicit DevBuf(void* p) : ptr(p) {}
+  ~DevBuf() { if (ptr) cudaFree(ptr); }
+};
+
 struct TableSet {
   void* mem = nullptr;                 // device
+  std::shared_ptr<DevBuf> owner;
   std::map<int, size_t> off_f, off_d;  // N -> byte offset of [tw N][ph N]
   size_t bytes = 0;
 };
@@ -34,6 +44,7 @@ struct btmv_plan_s {
   btmv::FftDev fft_sym[btmv::MAX_D];    // per dim, FP64, N = n_m
   // symbol
   void* sym = nullptr;
+  std::shared_ptr<btmv::DevBuf> sym_owner;
   size_t sym_bytes = 0;
   btmv::SymDev symdev;
   bool has_sym = false;

@@ -44,14 +44,23 @@ class SolveSpec:
         self.arrival = float(arrival)
         self.name = name
 
+    @property
+    def op_key(self):
+        """Solves with equal keys apply the same operator T and share its
+        resident symbol."""
+        return (self.n, self.c, id(self.t), self.sym_flags)
+
+    def symbol_footprint(self) -> int:
+        compressed = bool(self.sym_flags & bt.BTMV_SYM_PARITY)
+        return A.symbol_bytes(self.n, self.c, 8, bool(self.sym_flags & bt.BTMV_SYM_BLOCK), compressed) + 64 * 1024
+
     def footprint(self, nvec=9) -> int:
-        """Device bytes of an admitted solve: symbol, workspace, twiddles and
-        nvec vectors (matvec input/output plus the BiCGSTAB vectors)."""
+        """Device bytes of one admitted solve on an operator already resident:
+        workspace and nvec vectors (matvec input/output plus the BiCGSTAB
+        vectors)."""
         d = len(self.n)
         V = A.vector_bytes(self.n, self.c, 1, 8)
-        compressed = bool(self.sym_flags & bt.BTMV_SYM_PARITY)
-        sym = A.symbol_bytes(self.n, self.c, 8, bool(self.sym_flags & bt.BTMV_SYM_BLOCK), compressed)
-        return sym + (d - 1) * V + nvec * V + 64 * 1024
+        return (d - 1) * V + nvec * V
 
 
 class Solve:
@@ -144,11 +153,18 @@ class Server:
         self.batched = batched
         self.record = record          # optional: {solve name: [(x, y), ...]} filled with matvec pairs
         self.streams = [torch.cuda.Stream() for _ in range(self.max_inflight)]
+        self.ops = {}                 # operator key -> master plan holding the shared symbol
+
+    def _cost(self, spec):
+        return spec.footprint() + (0 if spec.op_key in self.ops else spec.symbol_footprint())
 
     def _admit(self, spec):
-        p = bt.Plan(spec.n, spec.c, bt.BTMV_C64, self.algo, max_rhs=1)
-        p.set_kernel(spec.t, spec.sym_flags, spec.parity)
-        return Solve(spec, p, self.torch, self.algo)
+        # one resident symbol per operator; each solve gets a clone (own workspace)
+        if spec.op_key not in self.ops:
+            master = bt.Plan(spec.n, spec.c, bt.BTMV_C64, self.algo, max_rhs=1)
+            master.set_kernel(spec.t, spec.sym_flags, spec.parity)
+            self.ops[spec.op_key] = master
+        return Solve(spec, self.ops[spec.op_key].clone(1), self.torch, self.algo)
 
     def run(self, specs):
         th = self.torch
@@ -168,15 +184,15 @@ class Server:
         while pending or active or inflight:
             now = time.perf_counter() - t0
             # admission by arrival time and HBM budget
-            while pending and pending[0].arrival <= now and used + pending[0].footprint() <= self.budget:
+            while pending and pending[0].arrival <= now and used + self._cost(pending[0]) <= self.budget:
                 spec = pending.popleft()
+                used += self._cost(spec)
                 s = self._admit(spec)
-                used += spec.footprint()
                 s.step()                                     # first request
                 active.append(s)
                 ready.append(s)
                 t_ready[id(s)] = time.perf_counter()
-            if pending and not active and not inflight and pending[0].footprint() > self.budget:
+            if pending and not active and not inflight and used + self._cost(pending[0]) > self.budget:
                 raise RuntimeError(f"solve {pending[0].name} does not fit the HBM budget")
             peak_active = max(peak_active, len(active))
             # completions
@@ -220,6 +236,9 @@ class Server:
         wall = time.perf_counter() - t0
         for s in finished:
             s.plan.close()
+        for m in self.ops.values():
+            m.close()
+        self.ops = {}
         lat_ms = np.array(lat) * 1e3
         return {
             "matvecs": matvecs, "wall_s": wall, "matvecs_per_s": matvecs / wall,
@@ -232,10 +251,10 @@ class Server:
         }
 
 
-def scaled_alpha(spec_t, parity, sym_flags, n, c):
-    """alpha = 0.5 / max over frequencies of |symbol| (spectral norm bound of
-    the scalar or per-block maximum), so that ||alpha T|| <= 1/2 and
-    BiCGSTAB on I - alpha T converges quickly.  Computed from the library's
+def scaled_alpha(spec_t, parity, sym_flags, n, c, target=0.5):
+    """alpha = target / (c max over frequencies of |symbol entry|), a bound on
+    the spectral norm of T, so that ||alpha T|| <= target < 1 and BiCGSTAB on
+    I - alpha T converges.  Computed from the library's
     own symbol (full 2n-grid transform scaled back to the unnormalised
     coefficients)."""
     p = bt.Plan(n, c, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT)
@@ -243,4 +262,4 @@ def scaled_alpha(spec_t, parity, sym_flags, n, c):
     S = bt.btmv_get_symbol(p.handle)
     p.close()
     scale = float(np.prod([2 * m for m in n]))
-    return 0.5 / (c * float(np.abs(S).max()) * scale)
+    return target / (c * float(np.abs(S).max()) * scale)

@@ -195,3 +195,31 @@ def test_register_kernels_vs_oracle_and_generic(n, c, algo):
     yg = yd.cpu().numpy().astype(np.complex128)
     assert rel(yg, ref) <= 1e-5
     assert rel(y, yg) <= 2e-6
+
+
+def test_plan_clone_shares_the_symbol():
+    n, c = (10, 12, 8), 3
+    t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    master = bt.Plan(n, c, 0)
+    master.set_kernel(t_orth, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+    clone = master.clone(max_rhs=2)
+    info_m, info_c = master.info, clone.info
+    assert info_c["has_symbol"] == 1 and info_c["symbol_bytes"] == info_m["symbol_bytes"]
+    assert info_c["max_rhs"] == 2
+    x = W.random_vector(n, c, seed=15, nrhs=2)
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    ym, yc = torch.zeros_like(xd), torch.zeros_like(xd)
+    master.apply(xd[:1], ym[:1], 1)
+    master.close()                          # the clone keeps the shared symbol alive
+    clone.apply(xd, yc, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(ym[:1], yc[:1])
+    ref = OE.embed_matvec(W.orthant_to_full(t_orth, par), round_input(x, 0))
+    assert rel(yc.cpu().numpy().astype(np.complex128), ref) <= 1e-5
+    # a new generator on the clone builds its own symbol
+    t2 = W.random_generator(n, c, seed=16)
+    clone.set_kernel(t2)
+    clone.apply(xd, yc, 2)
+    torch.cuda.synchronize()
+    assert rel(yc.cpu().numpy().astype(np.complex128), OE.embed_matvec(t2, round_input(x, 0))) <= 1e-5
+    clone.close()

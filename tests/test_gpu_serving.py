@@ -83,7 +83,8 @@ def test_solution_solves_the_system_by_the_oracle():
 
 def test_admission_respects_the_hbm_budget():
     specs = make_specs([((16, 16, 16), 3)] * 4, arrival_gap=0.0)
-    budget = specs[0].footprint() * 2 + 1            # room for two solves at a time
+    # room for the shared symbol and two solves at a time
+    budget = specs[0].symbol_footprint() + specs[0].footprint() * 2 + 1
     out = serve.Server(budget_bytes=budget).run(specs)
     assert out["solves"] == 4
     assert out["peak_active_solves"] <= 2
