@@ -509,7 +509,7 @@ def run_serving(args):
                         batched=False).run(specs)
     if rank != 0:
         return
-    strip = lambda r: {k: v for k, v in r.items() if k != "solutions"}  # noqa: E731
+    strip = lambda r: {k: v for k, v in r.items() if k not in ("solutions", "rhs")}  # noqa: E731
     line = {"metric": "served block Toeplitz matvecs/s (200 concurrent BiCGSTAB solves, complex64)",
             "value": res["matvecs_per_s"], "unit": "matvecs/s", "n_gpus": ws, "steps": res["matvecs"],
             "warmup": 0, "ms_per_step": 1000.0 * res["wall_s"] / max(1, res["matvecs"]),

@@ -65,7 +65,11 @@ class SolveSpec:
 
 class Solve:
     """BiCGSTAB state machine; each call of ``step`` consumes the last matvec
-    result and returns True when it has put a new request in ``self.xin``."""
+    result and returns True when it has put a new request in ``self.xin``.
+
+    The recurrence scalars stay on the device (no host synchronisation in a
+    step); the residual norm of each iteration is copied to pinned host
+    memory asynchronously and tested one iteration later."""
 
     def __init__(self, spec: SolveSpec, plan, torch, algo):
         self.spec = spec
@@ -73,59 +77,65 @@ class Solve:
         self.torch = torch
         shape = (1, spec.c) + spec.n
         dev = "cuda"
-        g = np.random.default_rng(spec.b_seed)
-        b = (g.standard_normal(shape) + 1j * g.standard_normal(shape)).astype(np.complex64)
-        self.b = torch.from_numpy(b).to(dev)
+        g = torch.Generator(device=dev)
+        g.manual_seed(spec.b_seed)                 # seeded right-hand side, drawn on the device
+        self.b = torch.randn(shape, generator=g, dtype=torch.complex64, device=dev)
         z = lambda: torch.zeros(shape, dtype=torch.complex64, device=dev)  # noqa: E731
         self.xin, self.yout = z(), z()
         self.x = z()
         self.r = self.b.clone()
         self.r0 = self.b.clone()
         self.p, self.v, self.s, self.tv = z(), z(), z(), z()
-        self.rho = self.alpha_k = self.omega = 1.0 + 0j
-        self.bnorm = float(torch.linalg.vector_norm(self.b))
+        one = torch.ones((), dtype=torch.complex64, device=dev)
+        self.rho, self.alpha_k, self.omega = one.clone(), one.clone(), one.clone()
+        self.bnorm = torch.linalg.vector_norm(self.b)
+        self.res_host = torch.zeros((), dtype=torch.float32).pin_memory()
+        self.res_host.fill_(1.0)
+        self.res_ev = None
         self.phase = "start"
         self.matvecs = 0
         self.done = False
         self.resid = 1.0
-        self.history = []
         self.algo = algo
 
-    # A w = w - alpha T w, with T w the last matvec result
-    def _apply_A(self, w, tw):
-        return w - self.spec.alpha * tw
+    @staticmethod
+    def _safe_div(th, a, b):
+        return th.where(b != 0, a / th.where(b != 0, b, th.ones_like(b)), th.zeros_like(a))
 
     def step(self) -> bool:
         th = self.torch
+        vd = lambda a, b: th.vdot(a.flatten(), b.flatten())  # noqa: E731
+        al = self.spec.alpha
         if self.phase == "start":
-            self.rho = complex(th.vdot(self.r0.flatten(), self.r.flatten()))
+            self.rho = vd(self.r0, self.r)
             self.p.copy_(self.r)
             self.xin.copy_(self.p)
             self.phase = "v"
             return True
-        if self.phase == "v":                      # yout = T p
-            self.v = self._apply_A(self.p, self.yout)
-            den = complex(th.vdot(self.r0.flatten(), self.v.flatten()))
-            self.alpha_k = self.rho / den if den != 0 else 0.0
+        if self.phase == "v":                      # yout = T p  ->  v = A p
+            self.v = self.p - al * self.yout
+            self.alpha_k = self._safe_div(th, self.rho, vd(self.r0, self.v))
             self.s = self.r - self.alpha_k * self.v
-            if float(th.linalg.vector_norm(self.s)) <= self.spec.tol * self.bnorm:
-                self.x += self.alpha_k * self.p
-                return self._finish(float(th.linalg.vector_norm(self.s)))
             self.xin.copy_(self.s)
             self.phase = "t"
             return True
-        if self.phase == "t":                      # yout = T s
-            self.tv = self._apply_A(self.s, self.yout)
-            tt = float(th.vdot(self.tv.flatten(), self.tv.flatten()).real)
-            self.omega = complex(th.vdot(self.tv.flatten(), self.s.flatten())) / tt if tt > 0 else 0.0
+        if self.phase == "t":                      # yout = T s  ->  t = A s
+            self.tv = self.s - al * self.yout
+            tt = vd(self.tv, self.tv)
+            self.omega = self._safe_div(th, vd(self.tv, self.s), tt)
             self.x += self.alpha_k * self.p + self.omega * self.s
             self.r = self.s - self.omega * self.tv
-            res = float(th.linalg.vector_norm(self.r)) / self.bnorm
-            self.history.append(res)
-            if res <= self.spec.tol or self.matvecs + 2 > self.spec.max_matvecs:
-                return self._finish(res * self.bnorm)
-            rho_new = complex(th.vdot(self.r0.flatten(), self.r.flatten()))
-            beta = (rho_new / self.rho) * (self.alpha_k / self.omega) if self.rho != 0 and self.omega != 0 else 0.0
+            # the previous iteration's residual, if its copy has landed
+            prev = float(self.res_host) if (self.res_ev is not None and self.res_ev.query()) else 1.0
+            res = th.linalg.vector_norm(self.r) / self.bnorm
+            self.res_host.copy_(res, non_blocking=True)
+            self.res_ev = th.cuda.Event()
+            self.res_ev.record()
+            if prev <= self.spec.tol or self.matvecs + 2 > self.spec.max_matvecs:
+                self.res_ev.synchronize()
+                return self._finish(float(self.res_host))
+            rho_new = vd(self.r0, self.r)
+            beta = self._safe_div(th, rho_new, self.rho) * self._safe_div(th, self.alpha_k, self.omega)
             self.rho = rho_new
             self.p = self.r + beta * (self.p - self.omega * self.v)
             self.xin.copy_(self.p)
@@ -133,8 +143,8 @@ class Solve:
             return True
         return False
 
-    def _finish(self, rnorm):
-        self.resid = rnorm / self.bnorm
+    def _finish(self, res):
+        self.resid = res
         self.done = True
         return False
 
@@ -153,6 +163,7 @@ class Server:
         self.batched = batched
         self.record = record          # optional: {solve name: [(x, y), ...]} filled with matvec pairs
         self.streams = [torch.cuda.Stream() for _ in range(self.max_inflight)]
+        self.upd = torch.cuda.Stream()  # Krylov updates: waits only on the batch whose results it reads
         self.ops = {}                 # operator key -> master plan holding the shared symbol
 
     def _cost(self, spec):
@@ -187,8 +198,9 @@ class Server:
             while pending and pending[0].arrival <= now and used + self._cost(pending[0]) <= self.budget:
                 spec = pending.popleft()
                 used += self._cost(spec)
-                s = self._admit(spec)
-                s.step()                                     # first request
+                with th.cuda.stream(self.upd):
+                    s = self._admit(spec)
+                    s.step()                                 # first request
                 active.append(s)
                 ready.append(s)
                 t_ready[id(s)] = time.perf_counter()
@@ -200,12 +212,15 @@ class Server:
                 ev, batch, _ = inflight.popleft()
                 ev.synchronize()
                 tdone = time.perf_counter()
+                self.upd.wait_event(ev)
                 for s in batch:
                     lat.append(tdone - t_ready.pop(id(s)))
                     s.matvecs += 1
                     if self.record is not None and s.spec.name in self.record:
                         self.record[s.spec.name].append((s.xin.clone(), s.yout.clone()))
-                    if s.step():
+                    with th.cuda.stream(self.upd):
+                        more = s.step()
+                    if more:
                         ready.append(s)
                         t_ready[id(s)] = time.perf_counter()
                     elif s.done:
@@ -216,7 +231,7 @@ class Server:
             if ready and len(inflight) < self.max_inflight:
                 batch, ready = ready, []
                 st = self.streams[nbatches % self.max_inflight]
-                st.wait_stream(th.cuda.current_stream())     # Krylov updates done
+                st.wait_stream(self.upd)                     # the batch reads the updated inputs
                 if self.batched:
                     bt.btmv_apply_batched([s.plan.handle for s in batch], [s.xin for s in batch],
                                           [s.yout for s in batch], [1] * len(batch), stream=st)
@@ -225,7 +240,6 @@ class Server:
                         bt.btmv_apply(s.plan.handle, s.xin, s.yout, 1, stream=st)
                 ev = th.cuda.Event()
                 ev.record(st)
-                th.cuda.current_stream().wait_event(ev)
                 inflight.append((ev, batch, time.perf_counter()))
                 nbatches += 1
                 batch_sizes.append(len(batch))
@@ -248,6 +262,7 @@ class Server:
             "peak_active_solves": peak_active, "solves": len(finished),
             "max_residual": max((s.resid for s in finished), default=0.0),
             "solutions": {s.spec.name: s.x for s in finished},
+            "rhs": {s.spec.name: s.b for s in finished},
         }
 
 
