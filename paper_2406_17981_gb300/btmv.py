@@ -158,9 +158,9 @@ def btmv_batch_tuning(plans, xs, ys, nrhs) -> dict:
     X = (ctypes.c_void_p * max(1, k))(*[_ptr(x) for x in xs])
     Y = (ctypes.c_void_p * max(1, k))(*[_ptr(y) for y in ys])
     R = (ctypes.c_int * max(1, k))(*[int(r) for r in nrhs])
-    out = (ctypes.c_int * 7)()
+    out = (ctypes.c_int * 8)()
     _check(lib().btmv_batch_tuning(k, P, X, Y, R, out))
-    keys = ("tile_lines", "leaf_lines", "leaf_rhs", "radix_order", "stages", "items", "blocks")
+    keys = ("tile_lines", "leaf_lines", "leaf_rhs", "radix_order", "stages", "items", "blocks", "mode")
     return dict(zip(keys, list(out)))
 
 

@@ -36,16 +36,19 @@ using namespace btmv;
 namespace {
 
 struct TuneCfg {
+  int mode = 0;    // 0: one persistent kernel; 1: graph with one branch per problem
   int TL = 0;      // strided-pass tile lines (0 = default)
   int Lt = 0;      // leaf lines per tile (0 = default)
   int rq = 0;      // leaf right-hand sides per tile (0 = default)
   int radix = 0;   // 0: radix-16 first, 1: radix-8 first
   std::string str() const {
     char b[64];
-    snprintf(b, sizeof b, "%d %d %d %d", TL, Lt, rq, radix);
+    snprintf(b, sizeof b, "%d %d %d %d %d", mode, TL, Lt, rq, radix);
     return b;
   }
 };
+
+constexpr int kBranchStreams = 16;
 
 struct Entry {
   std::vector<btmv_plan> plans;
@@ -63,8 +66,14 @@ struct Entry {
   int* h_err = nullptr;               // pinned copy of ctl->error after each launch
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev = nullptr;
+  // mode 1: branch streams and fork / join events
+  cudaStream_t bst[kBranchStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kBranchStreams] = {};
   bool launched = false;
   unsigned long long lru = 0;
+  int cfg_mode = 0;                   // mode of the stage table / graph in place
+  void* h_err_dev() const { return &((BatchCtl*)d_ctl)->error; }
 };
 
 std::mutex g_mu;
@@ -75,6 +84,11 @@ bool g_tune_loaded = false;
 
 void free_entry(Entry* e) {
   if (e->ev) { cudaEventSynchronize(e->ev); cudaEventDestroy(e->ev); }
+  for (int i = 0; i < kBranchStreams; ++i) {
+    if (e->bst[i]) cudaStreamDestroy(e->bst[i]);
+    if (e->join[i]) cudaEventDestroy(e->join[i]);
+  }
+  if (e->fork) cudaEventDestroy(e->fork);
   if (e->exec) cudaGraphExecDestroy(e->exec);
   if (e->d_stages) cudaFree(e->d_stages);
   if (e->d_ctl) cudaFree(e->d_ctl);
@@ -113,7 +127,7 @@ void load_tune_file() {
     if (!tab) continue;
     *tab = 0;
     TuneCfg c;
-    if (sscanf(tab + 1, "%d %d %d %d", &c.TL, &c.Lt, &c.rq, &c.radix) == 4) g_tuned[line] = c;
+    if (sscanf(tab + 1, "%d %d %d %d %d", &c.mode, &c.TL, &c.Lt, &c.rq, &c.radix) == 5) g_tuned[line] = c;
   }
   fclose(f);
 }
@@ -179,9 +193,10 @@ btmv_status build_stages(const Entry& e, const TuneCfg& cfg, std::vector<BatchSt
 }
 
 btmv_status upload(Entry& e, const TuneCfg& cfg) {
+  e.cfg_mode = cfg.mode;
   std::vector<BatchStage> st;
   size_t smem = 0;
-  build_stages(e, cfg, st, smem);
+  if (cfg.mode == 0) build_stages(e, cfg, st, smem);
   if (e.d_stages) { cudaFree(e.d_stages); e.d_stages = nullptr; }
   if (e.d_ctl) { cudaFree(e.d_ctl); e.d_ctl = nullptr; }
   e.nstages = (int)st.size();
@@ -203,8 +218,39 @@ btmv_status upload(Entry& e, const TuneCfg& cfg) {
   return BTMV_OK;
 }
 
+// Mode 1: every problem's own schedule (register-resident kernels where they
+// apply) on one of kBranchStreams streams forked from st and joined back.
+btmv_status enqueue_branches(Entry& e, cudaStream_t st) {
+  if (!e.fork) {
+    if (cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming) != cudaSuccess)
+      return fail(BTMV_E_CUDA, "apply_batched: fork event");
+    for (int i = 0; i < kBranchStreams; ++i)
+      if (cudaStreamCreateWithFlags(&e.bst[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&e.join[i], cudaEventDisableTiming) != cudaSuccess)
+        return fail(BTMV_E_CUDA, "apply_batched: branch streams");
+  }
+  cudaEventRecord(e.fork, st);
+  const int nb = std::min<int>(kBranchStreams, (int)e.plans.size());
+  for (int i = 0; i < nb; ++i) cudaStreamWaitEvent(e.bst[i], e.fork, 0);
+  for (size_t i = 0; i < e.plans.size(); ++i) {
+    if (!e.nrhs[i]) continue;
+    btmv_status s = btmv_apply_on_device(e.plans[i], e.x[i], e.y[i], e.nrhs[i], e.bst[i % nb]);
+    if (s != BTMV_OK) return s;
+  }
+  for (int i = 0; i < nb; ++i) {
+    cudaEventRecord(e.join[i], e.bst[i]);
+    cudaStreamWaitEvent(st, e.join[i], 0);
+  }
+  cudaError_t ce = cudaMemsetAsync(e.h_err_dev(), 0, sizeof(int), st);
+  if (ce != cudaSuccess) return fail(BTMV_E_CUDA, "apply_batched: status reset: %s", cudaGetErrorString(ce));
+  ce = cudaMemcpyAsync(e.h_err, e.h_err_dev(), sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (ce != cudaSuccess) return fail(BTMV_E_CUDA, "apply_batched: status copy: %s", cudaGetErrorString(ce));
+  return BTMV_OK;
+}
+
 // Enqueue one run: reset the control words, launch, copy the error word back.
 btmv_status enqueue(Entry& e, cudaStream_t st) {
+  if (e.cfg_mode == 1) return enqueue_branches(e, st);
   const size_t ctl_bytes = sizeof(BatchCtl) + std::max(1, e.nstages) * sizeof(unsigned);
   cudaError_t ce = cudaMemsetAsync(e.d_ctl, 0, ctl_bytes, st);
   if (ce != cudaSuccess) return fail(BTMV_E_CUDA, "apply_batched: reset: %s", cudaGetErrorString(ce));
@@ -245,10 +291,16 @@ float time_cfg(Entry& e, const TuneCfg& cfg, cudaStream_t st) {
   return best;
 }
 
-// Coordinate descent over tile lines, leaf lines, leaf rhs and radix order.
+// Execution mode first (persistent kernel or graph branches), then
+// coordinate descent over tile lines, leaf lines, leaf rhs and radix order
+// for the persistent kernel.
 TuneCfg autotune(Entry& e, cudaStream_t st) {
   TuneCfg best;
   float bt = time_cfg(e, best, st);
+  TuneCfg br;
+  br.mode = 1;
+  const float tb = time_cfg(e, br, st);
+  if (tb < bt) return br;
   int maxr = 1;
   for (int r : e.nrhs) maxr = std::max(maxr, r);
   const std::vector<std::vector<int>> cand = {{8, 16, 32}, {1, 2, 4, 8}, {1, 2, 4, 8, 16}, {0, 1}};
@@ -328,6 +380,34 @@ extern "C" BTMV_API btmv_status btmv_apply_batched(int count, const btmv_plan* p
     if (plans[i]->algo != BTMV_ALGO_SPLIT || plans[i]->prec != plans[0]->prec) persistent = false;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  if (getenv("BTMV_BATCH_DIRECT")) {
+    // argument sets that change every call (serving ticks): fork every
+    // problem's schedule onto a pool of streams and join, without a graph
+    static std::mutex mu;
+    static cudaStream_t pool[kBranchStreams] = {};
+    static cudaEvent_t fork = nullptr, join[kBranchStreams] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (!fork) {
+      cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+      for (int i = 0; i < kBranchStreams; ++i) {
+        cudaStreamCreateWithFlags(&pool[i], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+      }
+    }
+    const int nb = std::min(kBranchStreams, count);
+    cudaEventRecord(fork, st);
+    for (int i = 0; i < nb; ++i) cudaStreamWaitEvent(pool[i], fork, 0);
+    for (int i = 0; i < count; ++i)
+      if (nrhs[i]) {
+        btmv_status s = btmv_apply_on_device(plans[i], x[i], y[i], nrhs[i], pool[i % nb]);
+        if (s != BTMV_OK) return s;
+      }
+    for (int i = 0; i < nb; ++i) {
+      cudaEventRecord(join[i], pool[i]);
+      cudaStreamWaitEvent(st, join[i], 0);
+    }
+    return BTMV_OK;
+  }
   if (!persistent || getenv("BTMV_BATCH_SEQUENTIAL")) {
     // mixed precisions or plain-embedding plans: one apply after the other
     for (int i = 0; i < count; ++i)
@@ -368,10 +448,12 @@ extern "C" BTMV_API btmv_status btmv_apply_batched(int count, const btmv_plan* p
     *e->h_err = 0;
     const std::string sig = signature(*e);
     auto it = g_tuned.find(sig);
-    if (it != g_tuned.end()) {
-      e->cfg = it->second;
-    } else if (getenv("BTMV_NO_AUTOTUNE")) {
+    if (getenv("BTMV_NO_AUTOTUNE")) {
       e->cfg = TuneCfg();
+      const char* m = getenv("BTMV_BATCH_MODE");
+      e->cfg.mode = (m && atoi(m) == 1) ? 1 : 0;
+    } else if (it != g_tuned.end()) {
+      e->cfg = it->second;
     } else {
       e->cfg = autotune(*e, st);
       g_tuned[sig] = e->cfg;
@@ -402,6 +484,7 @@ extern "C" BTMV_API btmv_status btmv_batch_tuning(int count, const btmv_plan* pl
   std::lock_guard<std::mutex> lk(g_mu);
   Entry* e = find_entry(count, plans, x, y, nrhs);
   if (!e) return fail(BTMV_E_STATE, "batch_tuning: no batch with these arguments has run");
+  cfg_out[7] = e->cfg.mode;
   cfg_out[0] = e->cfg.TL; cfg_out[1] = e->cfg.Lt; cfg_out[2] = e->cfg.rq; cfg_out[3] = e->cfg.radix;
   cfg_out[4] = e->nstages; cfg_out[5] = (int)std::min<long long>(e->nitems, 0x7fffffff); cfg_out[6] = e->grid;
   return BTMV_OK;

@@ -180,7 +180,7 @@ class Server:
     def run(self, specs):
         th = self.torch
         if self.batched:
-            os.environ.setdefault("BTMV_NO_AUTOTUNE", "1")     # request mixes change every tick
+            os.environ.setdefault("BTMV_BATCH_DIRECT", "1")    # request mixes change every tick
         pending = collections.deque(sorted(specs, key=lambda s: s.arrival))
         active, ready = [], []
         inflight = collections.deque()                       # (event, [solves], t_launch)

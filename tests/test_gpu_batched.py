@@ -75,7 +75,9 @@ def test_batched_matches_oracle_and_single_apply(precision):
         for a, b in zip(out, again):
             assert np.array_equal(a, b)
         cfg = bt.btmv_batch_tuning([p.handle for p in plans], xs, ys, [x.shape[0] for x in xs])
-        assert cfg["stages"] == sum(8 for _ in SMALL) and cfg["blocks"] >= 1
+        assert cfg["mode"] in (0, 1)
+        if cfg["mode"] == 0:
+            assert cfg["stages"] == sum(8 for _ in SMALL) and cfg["blocks"] >= 1
     finally:
         for p in plans:
             p.close()
@@ -154,6 +156,35 @@ def test_persistent_wait_limit_reports_timeout_and_context_survives():
         t_orth, par, xh = refs_in[0]
         ref = OE.embed_matvec(W.orthant_to_full(t_orth, par), round_input(xh, 0))
         assert rel(out[0], ref) <= 1e-5
+    finally:
+        for p in plans:
+            p.close()
+
+
+@pytest.mark.parametrize("mode", ["persistent", "branches", "direct"])
+def test_each_batched_execution_mode(mode, monkeypatch):
+    """Every execution mode of btmv_apply_batched gives each problem's own
+    result: the persistent kernel (tuning off), the graph of branches, and
+    the direct stream fork used by the server."""
+    if mode in ("persistent", "branches"):
+        monkeypatch.setenv("BTMV_NO_AUTOTUNE", "1")
+        monkeypatch.setenv("BTMV_BATCH_MODE", "0" if mode == "persistent" else "1")
+    else:
+        monkeypatch.setenv("BTMV_BATCH_DIRECT", "1")
+    insts = [dict(SMALL[k], x_seed=SMALL[k]["x_seed"] + 50 + 7 * len(mode)) for k in range(len(SMALL))]
+    plans, xs, ys, refs_in = make_batch(insts)
+    try:
+        out = run_batch(plans, xs, ys)
+        for p, x, y in zip(plans, xs, out):
+            ya = torch.zeros_like(x)
+            p.apply(x, ya, x.shape[0])
+            torch.cuda.synchronize()
+            assert rel(y, ya.cpu().numpy().astype(np.complex128)) <= 1e-5
+        if mode != "direct":
+            cfg = bt.btmv_batch_tuning([p.handle for p in plans], xs, ys, [x.shape[0] for x in xs])
+            assert cfg["mode"] == (0 if mode == "persistent" else 1)
+            if mode == "persistent":
+                assert cfg["stages"] == 8 * len(insts)
     finally:
         for p in plans:
             p.close()
