@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS) + ["batched64", "serving200"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS) + ["batched64", "serving200", "multirhs"])
     ap.add_argument("--no-compare", action="store_true", help="skip the full-embedding and cuFFT rows")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
     return ap.parse_args()
@@ -220,6 +220,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving200":
         return run_serving(args)
+    if args.workload == "multirhs":
+        return run_multirhs(args)
     cfg = W.WORKLOADS[args.workload]
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
@@ -454,6 +456,59 @@ def run_batched(args):
                          "traffic": None, "algorithmic_bytes_per_step": tot_bytes},
             "sequential_btmv_apply": {"ms_per_step": seq_ms, "matvecs_per_s": pairs / (seq_ms / 1000.0)},
             "gpu_launches": args.steps, "clocks": clocks}
+    print(json.dumps(line))
+
+
+def run_multirhs(args):
+    """16 right-hand sides sharing one Green operator (d = 3, c = 3,
+    complex64): the default leaf (register kernels, one rhs per line group),
+    the shared-symbol CUDA-core contraction, and the tensor-core contraction.
+    Rates count rhs-matvecs per second."""
+    import torch
+
+    from paper_2406_17981_gb300 import btmv as bt
+    ws, rank, local = dist_setup(args)
+    out = {}
+    steps = max(5, min(args.steps, 200))
+    for n in ((64, 64, 64), (128, 128, 128)):
+        r = 16
+        t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+        x = torch.from_numpy(W.random_vector(n, 3, seed=31, nrhs=r).astype(np.complex64)).cuda()
+        ys = {}
+        for name, fl in (("register", 0), ("shared_rhs_cuda_core", bt.BTMV_FLAG_SHARED_RHS),
+                         ("tensor_core", bt.BTMV_FLAG_TENSOR_CORE)):
+            p = bt.Plan(n, 3, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=r, flags=fl | bt.BTMV_FLAG_PROFILE)
+            p.set_kernel(t_orth, 3, par)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                p.apply(x, y, r)
+            torch.cuda.synchronize()
+            bt.btmv_profile_read(p.handle)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                p.apply(x, y, r)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            prof = bt.btmv_profile_read(p.handle)
+            leaf_us = 1000 * prof["leaf"][0] / max(1, prof["leaf"][1])
+            ys[name] = y.cpu().numpy().astype(np.complex128)
+            out[f"{n[0]}^3 r{r} {name}"] = {"rhs_matvecs_per_s": r * 1000.0 / ms, "ms_per_step": ms,
+                                            "leaf_us_per_launch": leaf_us}
+            p.close()
+        ref = ys["register"]
+        for name in ("shared_rhs_cuda_core", "tensor_core"):
+            out[f"{n[0]}^3 r16 {name}"]["rel_diff_vs_register"] = float(
+                np.linalg.norm(ys[name] - ref) / np.linalg.norm(ref))
+    if rank != 0:
+        return
+    best = max(v["rhs_matvecs_per_s"] for k, v in out.items() if k.startswith("128"))
+    line = {"metric": "multi-rhs block Toeplitz rhs-matvecs/s (d=3 c=3 Green, 16 rhs, complex64)",
+            "value": best, "unit": "matvecs/s", "n_gpus": ws, "steps": steps, "warmup": 3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "multirhs", "nrhs": 16}, "variants": out}
     print(json.dumps(line))
 
 

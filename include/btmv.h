@@ -84,9 +84,17 @@ enum {
   BTMV_FLAG_NONE = 0,
   BTMV_FLAG_PROFILE = 1u << 0, /* record a CUDA event pair around every kernel
                                   launch of btmv_apply (see btmv_profile_read) */
-  BTMV_FLAG_GENERIC = 1u << 1  /* use only the generic shared-memory line kernels
+  BTMV_FLAG_GENERIC = 1u << 1, /* use only the generic shared-memory line kernels
                                   (any 7-smooth size, both precisions) instead of
                                   the register-resident power-of-two kernels   */
+  BTMV_FLAG_SHARED_RHS = 1u << 2,  /* multi-rhs leaf: all right-hand sides of a
+                                      line in one tile, each frequency's c x c
+                                      symbol block read once for all of them
+                                      (CUDA-core contraction)                  */
+  BTMV_FLAG_TENSOR_CORE = 1u << 3  /* as BTMV_FLAG_SHARED_RHS, with the c x c x
+                                      nrhs contraction on tensor cores (c = 3,
+                                      complex64, nrhs >= 2): TF32 mma with a
+                                      high/low split, FP32 accumulation        */
 };
 
 /*

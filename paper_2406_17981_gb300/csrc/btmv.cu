@@ -143,7 +143,8 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
   if (precision != BTMV_C64 && precision != BTMV_C128) return fail(BTMV_E_ARG, "plan_create: bad precision %d", precision);
   if (algo != BTMV_ALGO_SPLIT && algo != BTMV_ALGO_FULL) return fail(BTMV_E_ARG, "plan_create: bad algo %d", algo);
   if (max_rhs < 1) return fail(BTMV_E_ARG, "plan_create: max_rhs=%d < 1", max_rhs);
-  if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC)) return fail(BTMV_E_ARG, "plan_create: unknown flags 0x%x", flags);
+  if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC | BTMV_FLAG_SHARED_RHS | BTMV_FLAG_TENSOR_CORE))
+    return fail(BTMV_E_ARG, "plan_create: unknown flags 0x%x", flags);
   for (int m = 0; m < d; ++m) {
     if (n[m] < 1) return fail(BTMV_E_ARG, "plan_create: n[%d]=%d < 1", m, n[m]);
     const int N = algo == BTMV_ALGO_FULL ? 2 * n[m] : n[m];
@@ -191,7 +192,8 @@ extern "C" btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flag
   if (!src || !out) return fail(BTMV_E_ARG, "plan_clone: NULL argument");
   *out = nullptr;
   if (max_rhs < 1) return fail(BTMV_E_ARG, "plan_clone: max_rhs=%d < 1", max_rhs);
-  if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC)) return fail(BTMV_E_ARG, "plan_clone: unknown flags 0x%x", flags);
+  if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC | BTMV_FLAG_SHARED_RHS | BTMV_FLAG_TENSOR_CORE))
+    return fail(BTMV_E_ARG, "plan_clone: unknown flags 0x%x", flags);
   btmv_plan p = new btmv_plan_s();
   p->d = src->d; p->c = src->c; p->prec = src->prec; p->algo = src->algo; p->max_rhs = max_rhs; p->flags = flags;
   for (int m = 0; m < MAX_D; ++m) { p->n[m] = src->n[m]; p->fft_apply[m] = src->fft_apply[m]; p->fft_sym[m] = src->fft_sym[m]; }
@@ -519,10 +521,12 @@ LeafArgs btmv::leaf_step_args(btmv_plan p, int nrhs, int nn, const LeafNode* nod
 template <class T>
 static btmv_status leaf_launch(btmv_plan p, int nrhs, int nn, const LeafNode* nodes, bool full,
                                cudaStream_t st) {
-  LeafArgs la = leaf_step_args(p, nrhs, nn, nodes, full, sizeof(T), 0, 0);
+  const bool shared = (p->flags & (BTMV_FLAG_SHARED_RHS | BTMV_FLAG_TENSOR_CORE)) && nrhs > 1;
+  LeafArgs la = leaf_step_args(p, nrhs, nn, nodes, full, sizeof(T), 0, shared ? std::min(nrhs, 16) : 0);
+  la.tensor = (shared && (p->flags & BTMV_FLAG_TENSOR_CORE) && p->c == 3 && sizeof(T) == sizeof(float2)) ? 1 : 0;
   ProfScope ps(p, full ? BTMV_K_FULL_LEAF : BTMV_K_LEAF, st);
-  cudaError_t e = (!(p->flags & BTMV_FLAG_GENERIC) && leaf_reg_supported(la, sizeof(T))) ? launch_leaf_reg(la, st)
-                                                                                         : launch_leaf<T>(la, st);
+  const bool reg = !(p->flags & BTMV_FLAG_GENERIC) && !shared && leaf_reg_supported(la, sizeof(T));
+  cudaError_t e = reg ? launch_leaf_reg(la, st) : launch_leaf<T>(la, st);
   if (e != cudaSuccess) return fail(BTMV_E_CUDA, "leaf pass: %s", cudaGetErrorString(e));
   return BTMV_OK;
 }

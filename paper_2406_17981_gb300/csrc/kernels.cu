@@ -196,17 +196,17 @@ __device__ __forceinline__ long long sym_index(const SymDev& S, const int* f, in
   return S.cls_off[cls] + lin;
 }
 
+// c x c symbol multiply at every frequency of the tile, CUDA cores: each
+// frequency's block is loaded once and applied to all rq right-hand sides.
 template <class T>
 __device__ __forceinline__ void leaf_multiply(T* __restrict__ R, const LeafArgs& a, int b,
                                               const int* __restrict__ fpre, int ls) {
-  const int N = a.N, Lt = a.Lt, c = a.c;
-  const int total = a.rq * Lt * N;
+  const int N = a.N, Lt = a.Lt, c = a.c, rq = a.rq;
+  const int total = Lt * N;
   const T* __restrict__ S = (const T*)a.sym.data;
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int l = e % N;
-    const int rest = e / N;
-    const int li = rest % Lt;
-    const int q = rest / Lt;
+    const int li = e / N;
     if (fpre[li * 4 + 3] == 0) continue;   // line beyond the node
     int f[MAX_D];
     for (int m = 0; m < a.dl; ++m) f[m] = fpre[li * 4 + m];
@@ -214,20 +214,147 @@ __device__ __forceinline__ void leaf_multiply(T* __restrict__ R, const LeafArgs&
     int fold, cls;
     const long long base = sym_index(a.sym, f, fold, cls);
     const long long blk = a.sym.blk[cls];
-    T x[3], y[3];
-    for (int ai = 0; ai < c; ++ai) x[ai] = R[((q * c + ai) * Lt + li) * ls + l];
-    for (int ai = 0; ai < c; ++ai) {
-      T acc = czero<T>();
+    T sv[3][3];
+    for (int ai = 0; ai < c; ++ai)
       for (int bi = 0; bi < c; ++bi) {
         const int kk = a.sym.comp[ai][bi];
         T s = __ldg(&S[base + kk * blk]);
         if (__popc(a.sym.oddmask[kk] & fold) & 1) { s.x = -s.x; s.y = -s.y; }
-        acc = cadd(acc, cmul(s, x[bi]));
+        sv[ai][bi] = s;
       }
-      y[ai] = acc;
+    for (int q = 0; q < rq; ++q) {
+      T x[3], y[3];
+      for (int ai = 0; ai < c; ++ai) x[ai] = R[((q * c + ai) * Lt + li) * ls + l];
+      for (int ai = 0; ai < c; ++ai) {
+        T acc = czero<T>();
+        for (int bi = 0; bi < c; ++bi) acc = cadd(acc, cmul(sv[ai][bi], x[bi]));
+        y[ai] = acc;
+      }
+      for (int ai = 0; ai < c; ++ai) R[((q * c + ai) * Lt + li) * ls + l] = y[ai];
     }
-    for (int ai = 0; ai < c; ++ai) R[((q * c + ai) * Lt + li) * ls + l] = y[ai];
   }
+}
+
+// The same multiply on tensor cores for c = 3 and complex64 (mma.sync
+// m16n8k8, TF32 inputs, FP32 accumulation).  A warp takes two frequencies:
+// their 3x3 complex blocks, written as real 6x6 blocks [[Re, -Im], [Im, Re]],
+// sit block-diagonally in a 16x16 A tile; the columns of B are eight
+// right-hand sides, rows the real and imaginary parts of the three
+// components of both frequencies.  Each operand is split into a TF32 high
+// part and a TF32 remainder and the product is formed as
+// hi*hi + hi*lo + lo*hi, which keeps FP32-level accuracy.
+__device__ __forceinline__ unsigned f2tf32(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// element (row i, col j) of the real 6x6 block of a complex 3x3 matrix
+__device__ __forceinline__ float real_block(const float2 (&s)[3][3], int i, int j) {
+  const float2 v = s[i % 3][j % 3];
+  if ((i < 3) == (j < 3)) return v.x;     // Re on the diagonal blocks
+  return i < 3 ? -v.y : v.y;              // -Im upper right, Im lower left
+}
+
+__device__ __forceinline__ void leaf_multiply_tc(float2* __restrict__ R, const LeafArgs& a, int b,
+                                                 const int* __restrict__ fpre, int ls) {
+  const int N = a.N, Lt = a.Lt, rq = a.rq;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int nfreq = Lt * N;
+  const int npair = (nfreq + 1) / 2;
+  const float2* __restrict__ S = (const float2*)a.sym.data;
+  for (int pr = warp; pr < npair; pr += nwarp) {
+    // the two frequencies of this pair (the second may not exist)
+    int fl[2], fli[2];
+    bool fok[2];
+    float2 sv[2][3][3];
+    for (int h = 0; h < 2; ++h) {
+      const int e = 2 * pr + h;
+      fok[h] = e < nfreq;
+      fl[h] = fok[h] ? e % N : 0;
+      fli[h] = fok[h] ? e / N : 0;
+      if (fok[h] && fpre[fli[h] * 4 + 3] == 0) fok[h] = false;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) sv[h][i][j] = make_float2(0.f, 0.f);
+      if (!fok[h]) continue;
+      int f[MAX_D];
+      for (int m = 0; m < a.dl; ++m) f[m] = fpre[fli[h] * 4 + m];
+      f[a.dl] = a.split ? 2 * fl[h] + b : fl[h];
+      int fold, cls;
+      const long long base = sym_index(a.sym, f, fold, cls);
+      const long long blk = a.sym.blk[cls];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          const int kk = a.sym.comp[i][j];
+          float2 v = __ldg(&S[base + kk * blk]);
+          if (__popc(a.sym.oddmask[kk] & fold) & 1) { v.x = -v.x; v.y = -v.y; }
+          sv[h][i][j] = v;
+        }
+    }
+    // A fragments (two k-steps), split into TF32 high and low parts
+    unsigned ahi[2][4], alo[2][4];
+    for (int ks = 0; ks < 2; ++ks) {
+      const int rows[4] = {g, g + 8, g, g + 8};
+      const int cols[4] = {tq + 8 * ks, tq + 8 * ks, tq + 4 + 8 * ks, tq + 4 + 8 * ks};
+      for (int u = 0; u < 4; ++u) {
+        const int r = rows[u], k = cols[u];
+        float v = 0.f;
+        if (r < 12 && k < 12 && r / 6 == k / 6) v = real_block(sv[r / 6], r % 6, k % 6);
+        ahi[ks][u] = f2tf32(v);
+        alo[ks][u] = f2tf32(v - __uint_as_float(ahi[ks][u]));
+      }
+    }
+    // element of B / D: row k -> frequency k / 6, component (k % 6) % 3, part (k % 6) / 3
+    auto addr = [&](int k, int q) -> float* {
+      const int h = k / 6, comp = (k % 6) % 3, part = (k % 6) / 3;
+      float2* p = R + ((q * 3 + comp) * Lt + fli[h]) * ls + fl[h];
+      return part ? &p->y : &p->x;
+    };
+    for (int q0 = 0; q0 < rq; q0 += 8) {
+      const int qn = q0 + g;                       // this lane's B column / D column source
+      unsigned bhi[2][2], blo[2][2];
+      for (int ks = 0; ks < 2; ++ks)
+        for (int u = 0; u < 2; ++u) {
+          const int k = tq + 4 * u + 8 * ks;
+          float v = 0.f;
+          if (k < 12 && qn < rq && fok[k / 6]) v = *addr(k, qn);
+          bhi[ks][u] = f2tf32(v);
+          blo[ks][u] = f2tf32(v - __uint_as_float(bhi[ks][u]));
+        }
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int ks = 0; ks < 2; ++ks) {
+        mma_tf32(d, ahi[ks], bhi[ks]);
+        mma_tf32(d, ahi[ks], blo[ks]);
+        mma_tf32(d, alo[ks], bhi[ks]);
+      }
+      __syncwarp();                               // every lane has read its B values
+      const int rows[4] = {g, g, g + 8, g + 8};
+      const int colq[4] = {q0 + 2 * tq, q0 + 2 * tq + 1, q0 + 2 * tq, q0 + 2 * tq + 1};
+      for (int u = 0; u < 4; ++u) {
+        const int r = rows[u], q = colq[u];
+        if (r < 12 && q < rq && fok[r / 6]) *addr(r, q) = d[u];
+      }
+      __syncwarp();
+    }
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void leaf_multiply_any(T* __restrict__ R, const LeafArgs& a, int b,
+                                                  const int* __restrict__ fpre, int ls) {
+  if constexpr (sizeof(T) == sizeof(float2)) {
+    if (a.tensor && a.c == 3) { leaf_multiply_tc((float2*)R, a, b, fpre, ls); return; }
+  }
+  leaf_multiply<T>(R, a, b, fpre, ls);
 }
 
 template <class T>
@@ -280,7 +407,7 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, unsigned char* smem
 
   // even half (or the whole 2n line for the plain embedding)
   T* r = fft_lines<false, false>(B0, B1, NV, ls, 1, a.fft);
-  leaf_multiply<T>(r, a, 0, fpre, ls);
+  leaf_multiply_any<T>(r, a, 0, fpre, ls);
   __syncthreads();
   T* A0 = fft_lines<true, false>(r, (r == B0) ? B1 : B0, NV, ls, 1, a.fft);
   T* A1 = nullptr;
@@ -288,7 +415,7 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, unsigned char* smem
     // odd half: twiddled input in X, scratch = the buffer not holding A0
     T* S = (A0 == B0) ? B1 : B0;
     T* r1 = fft_lines<false, false>(X, S, NV, ls, 1, a.fft);
-    leaf_multiply<T>(r1, a, 1, fpre, ls);
+    leaf_multiply_any<T>(r1, a, 1, fpre, ls);
     __syncthreads();
     A1 = fft_lines<true, false>(r1, (r1 == X) ? S : X, NV, ls, 1, a.fft);
   }

@@ -77,6 +77,7 @@ struct LeafArgs {
   int dl;                    // number of line dims (d - 1)
   int ext[3];                // extents of the line dims
   int split;                 // 1: split halves f = 2 l + b; 0: full grid f = l
+  int tensor;                // 1: c x c x rq contraction on tensor cores (c = 3, complex64)
   long long tiles_per_node;
   int nnodes;
   LeafNode nodes[MAX_LEAF_NODES];

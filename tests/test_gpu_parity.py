@@ -223,3 +223,33 @@ def test_plan_clone_shares_the_symbol():
     torch.cuda.synchronize()
     assert rel(yc.cpu().numpy().astype(np.complex128), OE.embed_matvec(t2, round_input(x, 0))) <= 1e-5
     clone.close()
+
+
+@pytest.mark.parametrize("n,r", [((16, 20, 24), 9), ((32, 32, 32), 16), ((12, 60), 8)])
+@pytest.mark.parametrize("flag", ["shared", "tensor"])
+def test_multi_rhs_contraction_paths(n, r, flag):
+    """All right-hand sides of a line share each symbol read (CUDA cores), or
+    the c x c x nrhs contraction runs on tensor cores (TF32 high/low split):
+    both match the oracle within the complex64 gate and the default path."""
+    c = 3
+    if len(n) == 3:
+        t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+        flags_s = bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY
+        tf = W.orthant_to_full(t_orth, par)
+    else:
+        t_orth, par, flags_s = W.random_generator(n, c, seed=17), None, 0
+        tf = t_orth
+    x = W.random_vector(n, c, seed=18, nrhs=r)
+    pf = bt.BTMV_FLAG_SHARED_RHS if flag == "shared" else bt.BTMV_FLAG_TENSOR_CORE
+    plan = bt.Plan(n, c, 0, max_rhs=r, flags=pf)
+    plan.set_kernel(t_orth, flags_s, par)
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    yd = torch.zeros_like(xd)
+    plan.apply(xd, yd, r)
+    torch.cuda.synchronize()
+    plan.close()
+    y = yd.cpu().numpy().astype(np.complex128)
+    ref = OE.embed_matvec(tf, round_input(x, 0))
+    assert rel(y, ref) <= 1e-5
+    y0 = run_btmv(t_orth, x, n, c, 0, 0, flags_s, par)
+    assert rel(y, y0) <= 2e-6
