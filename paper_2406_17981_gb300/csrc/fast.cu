@@ -372,7 +372,10 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
   }
   float2* const lbase = smem_cg + (li * C) * CF::GS;   // spectra of this line's groups
 
-  const int nbr = a.split ? 2 : 1;
+  // FF kernels always run both halves (split leaves); unrolled so that the
+  // half index is a compile-time constant in the index arithmetic
+  const int nbr = FF ? 2 : (a.split ? 2 : 1);
+#pragma unroll(FF ? 2 : 1)
   for (int b = 0; b < nbr; ++b) {
     if (b) cp_async_wait_all();       // phase table staged
     __syncthreads();
@@ -398,12 +401,15 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-          float2 sv = hi ? rowb[kr[j] + (N - b - t - TT * m)] : rowb[kr[j] + (t + TT * m)];
+          const float2 sv = hi ? rowb[kr[j] + (N - b - t - TT * m)] : rowb[kr[j] + (t + TT * m)];
           const float sgn = hi ? sgf1[j] : sgf0[j];
-          sv.x *= sgn; sv.y *= sgn;
           const SmLine<PD, TT> sj{lbase + j * CF::GS};
           const float2 xv = (PD == TT) ? *sj.cyc(t, m) : sj.ld(t + TT * m);
-          acc = cadd(acc, cmul(sv, xv));
+          // acc += sgn * (sv * xv): the parity sign rides on the accumulating FMA
+          const float px = fmaf(sv.x, xv.x, -sv.y * xv.y);
+          const float py = fmaf(sv.x, xv.y, sv.y * xv.x);
+          acc.x = fmaf(sgn, px, acc.x);
+          acc.y = fmaf(sgn, py, acc.y);
         }
         w[m] = acc;
       }

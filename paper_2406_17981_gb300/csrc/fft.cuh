@@ -203,6 +203,16 @@ template <int RAD, bool INV, class T> __device__ __forceinline__ void dft(T* a) 
   else if constexpr (RAD == 16) dft16<INV>(a);
 }
 
+// Quotient x / d for 0 <= x < 2^22 through a float reciprocal: with inv the
+// rounded 1/d, (x + 0.5) * inv lies within 2^-23 relative of x/d + 0.5/d,
+// which is at least 0.5/d from the next integer, so truncation is exact.
+struct FDiv {
+  int d;
+  float inv;
+  __device__ __forceinline__ explicit FDiv(int d_) : d(d_), inv(1.0f / (float)d_) {}
+  __device__ __forceinline__ int div(int x) const { return (int)(((float)x + 0.5f) * inv); }
+};
+
 // ------------------------------------------------------------ FFT plan
 constexpr int MAX_STAGES = 12;
 
@@ -223,11 +233,12 @@ __device__ __forceinline__ void stage_smem(const T* __restrict__ src, T* __restr
   const int nb = N / RAD;      // butterflies per line
   const int mp = nb / L;       // N / (L * RAD)
   const int total = nl * nb;
+  const FDiv dnl(nl), dnb(nb), dmp(mp);
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     int line, j;
-    if (LF) { line = idx % nl; j = idx / nl; }
-    else    { j = idx % nb; line = idx / nb; }
-    const int f1 = j / mp;
+    if (LF) { j = dnl.div(idx); line = idx - j * nl; }
+    else    { line = dnb.div(idx); j = idx - line * nb; }
+    const int f1 = dmp.div(j);
     const T* s = src + line * ls;
     T* o = dst + line * ls;
     const int base = j + (RAD - 1) * mp * f1;

@@ -51,10 +51,11 @@ __device__ __forceinline__ void pass_load(T* __restrict__ d0, T* __restrict__ d1
   // d0 receives the line (times P when tw0), d1 (if non-null) receives P * line
   const int TL = g.TL, N = g.N;
   const int total = TL * N;
+  const FDiv dN(N), dTL(TL);
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     int line, k;
-    if (g.contig) { line = e / N; k = e - line * N; }
-    else          { line = e % TL; k = e / TL; }
+    if (g.contig) { line = dN.div(e); k = e - line * N; }
+    else          { k = dTL.div(e); line = e - k * TL; }
     T v = czero<T>();
     if ((okl[line] & 2) && k < m.len) v = src[off[line] + (long long)k * m.es];
     const int si = line * ls + k * es;
@@ -74,10 +75,11 @@ __device__ __forceinline__ void pass_store(T* __restrict__ dst, const T* __restr
                                            const PassGeom& g, int ls, int es, const T* __restrict__ ph) {
   const int TL = g.TL, N = g.N;
   const int total = TL * N;
+  const FDiv dN(N), dTL(TL);
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     int line, k;
-    if (g.contig) { line = e / N; k = e - line * N; }
-    else          { line = e % TL; k = e / TL; }
+    if (g.contig) { line = dN.div(e); k = e - line * N; }
+    else          { k = dTL.div(e); line = e - k * TL; }
     if (!(okl[line] & 1) || k >= m.len) continue;
     const int si = line * ls + k * es;
     T v = r0[si];
@@ -204,9 +206,10 @@ __device__ __forceinline__ void leaf_multiply(T* __restrict__ R, const LeafArgs&
   const int N = a.N, Lt = a.Lt, c = a.c, rq = a.rq;
   const int total = Lt * N;
   const T* __restrict__ S = (const T*)a.sym.data;
+  const FDiv dN(N);
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int l = e % N;
-    const int li = e / N;
+    const int li = dN.div(e);
+    const int l = e - li * N;
     if (fpre[li * 4 + 3] == 0) continue;   // line beyond the node
     int f[MAX_D];
     for (int m = 0; m < a.dl; ++m) f[m] = fpre[li * 4 + m];
@@ -390,13 +393,15 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, unsigned char* smem
 
   const T* __restrict__ in = (const T*)nd.in;
   const int totalv = NV * N;
+  const FDiv dN(N), dLt(Lt), dc(c);
   for (int e = threadIdx.x; e < totalv; e += blockDim.x) {
-    const int vl = e / N;
+    const int vl = dN.div(e);
     const int k = e - vl * N;
-    const int li = vl % Lt;
-    const int qa = vl / Lt;
-    const int ai = qa % c;
-    const int q = q0 + qa / c;
+    const int qa = dLt.div(vl);
+    const int li = vl - qa * Lt;
+    const int qq = dc.div(qa);
+    const int ai = qa - qq * c;
+    const int q = q0 + qq;
     T v = czero<T>();
     if (fpre[li * 4 + 3] && q < a.nrhs)
       v = in[(long long)q * a.rhs_stride + (long long)ai * a.comp_stride + (l0 + li) * N + k];
@@ -422,12 +427,13 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, unsigned char* smem
 
   T* __restrict__ out = (T*)nd.out;
   for (int e = threadIdx.x; e < totalv; e += blockDim.x) {
-    const int vl = e / N;
+    const int vl = dN.div(e);
     const int k = e - vl * N;
-    const int li = vl % Lt;
-    const int qa = vl / Lt;
-    const int ai = qa % c;
-    const int q = q0 + qa / c;
+    const int qa = dLt.div(vl);
+    const int li = vl - qa * Lt;
+    const int qq = dc.div(qa);
+    const int ai = qa - qq * c;
+    const int q = q0 + qq;
     if (!fpre[li * 4 + 3] || q >= a.nrhs) continue;
     T v = A0[vl * ls + k];
     if (A1) v = cadd(v, cmulc(A1[vl * ls + k], __ldg(&ph[k])));
