@@ -154,13 +154,21 @@ def barrier(ws):
 
 
 def max_over_ranks(v: float, ws: int) -> float:
+    """The slowest rank's time (all ranks get it)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(ws: int, units_per_rank: float, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank runs its own instance)."""
+    return ws * units_per_rank / (ms_max / 1000.0)
 
 
 def make_generator(cfg):
@@ -272,7 +280,7 @@ def main():
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, ws)
     prof = bt.btmv_profile_read(plan.handle)
-    value = ws * args.steps / (ms_max / 1000.0)
+    value = job_rate(ws, args.steps, ms_max)
     launches = info["launches_per_apply"] * args.steps
 
     # dominant kernel and its roofline (algorithmic bytes per launch / event time)
