@@ -1,0 +1,272 @@
+// Register-resident fused leaf pass for the line lengths fast.cuh provides
+// plans for.
+#include "fast.cuh"
+
+namespace btmv {
+
+// ------------------------------------------------------------------- leaf
+// One thread group of T threads per (line, component); a line's C groups
+// sit next to each other in the block.  Each group runs the even half, then
+// the odd half of the last level: forward FFT, spectrum to shared memory, the
+// row cc of the c x c symbol multiply (reading the other components'
+// spectra), inverse FFT.  The even result waits in a per-group stash until
+// the odd one is added with conj(P).  The plain embedding (a.split == 0)
+// runs a single 2n-point pass per line.
+template <class P, int C> struct LeafCfg {
+  // lines per block: 96 threads for c = 3, 128 for c = 1 (whole warps)
+  static constexpr int LPC = C == 1 ? 128 / P::T : 32 / P::T;
+  static constexpr int THREADS = LPC * C * P::T;
+  static constexpr int SPN = padded_len<P>();
+  static constexpr int BASE = SPN + P::N;                        // spectrum + stash
+  static constexpr int TGT = P::T < 16 ? P::T : 0;
+  static constexpr int GS = BASE + ((TGT - BASE % 16) + 16) % 16;  // group stride, = T mod 16
+  // staged symbol rows: stored block k of a line's row starts at
+  // k * JP + 8 * s(k) and lines are LS apart, chosen so that the rows two
+  // thread groups of a half-warp read together sit in opposite bank halves
+  static constexpr int JP = ((P::N / 2 + 1 + 8) + 15) / 16 * 16;
+  static __host__ __device__ constexpr int line_stride(int nsym) { return nsym * JP + 8; }
+  static constexpr int MINB = P::R3 == 1 ? (C == 1 ? 2 : (P::R1 <= 16 ? 5 : 2)) : 1; // blocks per SM to aim for
+  // dynamic smem: groups | phase table | staged symbol rows (nsym per line)
+  static size_t smem(int nsym) {
+    return ((size_t)LPC * C * GS + P::N + (size_t)LPC * line_stride(nsym)) * sizeof(float2);
+  }
+};
+
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <class P, int C, bool FF>
+__global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k_leaf_cg(const LeafArgs a) {
+  typedef LeafCfg<P, C> CF;
+  constexpr int R1 = P::R1, TT = P::T, N = P::N, PD = pad_div<P>(), JP = CF::JP;
+  extern __shared__ __align__(16) float2 smem_cg[];
+  const int gid = threadIdx.x / TT;           // group in block
+  const int t = threadIdx.x % TT;
+  const int li = gid / C;                     // line in block
+  const int cc = gid - li * C;                // component of this group
+  const int lt = threadIdx.x - li * C * TT;   // thread index within the line
+  float2* const gbuf = smem_cg + gid * CF::GS;
+  const SmLine<PD, TT> spec{gbuf};
+  float2* const stash = gbuf + CF::SPN;
+  float2* const phs = smem_cg + CF::LPC * C * CF::GS;           // phase table P (N values)
+  const SymDev& S = a.sym;
+  float2* const rowb = phs + N + li * CF::line_stride(S.nsym);    // staged symbol row of this line
+  const LeafNode nd = a.nodes[blockIdx.y];
+  const long long gline = (long long)blockIdx.x * CF::LPC + li;   // over (rhs, line)
+  const bool ok = gline < (long long)a.nrhs * a.lines;
+  const long long q = ok ? gline / a.lines : 0;
+  const long long line = ok ? gline - q * a.lines : 0;
+  const long long base = q * a.rhs_stride + cc * a.comp_stride + line * N + t;
+  const float2* __restrict__ tw = (const float2*)a.fft.tw;
+  const float2* __restrict__ ph = (const float2*)a.fft.ph;
+
+  // symbol addressing for this line
+  const int dl = a.dl;
+  int clsp = 0, foldp = 0;
+  long long lin = 0;
+  {
+    int fpre[MAX_D];
+    long long r = line;
+    for (int m = dl - 1; m >= 0; --m) {
+      const int im = (int)(r % a.ext[m]);
+      r /= a.ext[m];
+      fpre[m] = a.split ? 2 * im + ((nd.prefix >> m) & 1) : im;
+    }
+    for (int m = 0; m < dl; ++m) clsp = (clsp << 1) | (fpre[m] & 1);
+    for (int m = 0; m < dl; ++m) {
+      int fm = fpre[m];
+      if (S.compressed && fm > S.n[m]) { fm = 2 * S.n[m] - fm; foldp |= 1 << m; }
+      lin = lin * S.J[clsp << 1][m] + (fm >> 1);
+    }
+  }
+  const int nl = S.n[dl];
+  const float2* __restrict__ Sd = (const float2*)S.data;
+  // FF: split leaf on the mirror-compressed store with n_d == N; the line's
+  // row of each parity class is staged in shared memory while the
+  // transforms run
+  const int nsym = S.nsym;
+  // bank-half shift of each stored block of the c = 3 block-symmetric row:
+  // blocks 00 11 22 01 02 12 -> 0 0 0 1 0 1
+  auto row_pos = [&](int k) { return k * JP + ((C == 3 && nsym == 6 && (k == 3 || k == 5)) ? 8 : 0); };
+  auto stage_row = [&](int bb) {
+    if (!FF || !ok) return;
+    const int cl = (clsp << 1) | bb;
+    const int J = S.J[cl][dl];
+    const float2* src = Sd + S.cls_off[cl] + lin * J;
+    const long long blk = S.blk[cl];
+    for (int k = 0; k < nsym; ++k)
+      for (int j = lt; j < J; j += C * TT) cp_async8(rowb + row_pos(k) + j, src + k * blk + j);
+  };
+  for (int e = threadIdx.x; e < N; e += CF::THREADS) cp_async8(phs + e, ph + e);
+  stage_row(0);
+
+  TwReg<P> twr;
+  if constexpr (P::R3 == 1) twr.load(t, tw);
+
+  float2 xr[R1];
+  {
+    const float2* __restrict__ in = (const float2*)nd.in + base;
+#pragma unroll
+    for (int m = 0; m < R1; ++m) xr[m] = ok ? in[TT * m] : make_float2(0.f, 0.f);
+  }
+
+  long long off[2][C];
+  int kr[C];
+  unsigned sg0 = 0, sg1 = 0;      // sign bits of row cc without / with a fold of the last dim
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int k = S.comp[cc][j];
+    kr[j] = row_pos(k);
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb) {
+      const int cl = (clsp << 1) | bb;
+      off[bb][j] = S.cls_off[cl] + lin * S.J[cl][dl] + (long long)k * S.blk[cl];
+    }
+    sg0 |= (unsigned)(__popc(S.oddmask[k] & foldp) & 1) << j;
+    sg1 |= (unsigned)(__popc(S.oddmask[k] & (foldp | (1 << dl))) & 1) << j;
+  }
+  float sgf0[C], sgf1[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    sgf0[j] = ((sg0 >> j) & 1) ? -1.f : 1.f;
+    sgf1[j] = ((sg1 >> j) & 1) ? -1.f : 1.f;
+  }
+  float2* const lbase = smem_cg + (li * C) * CF::GS;   // spectra of this line's groups
+
+  // FF kernels always run both halves (split leaves); unrolled so that the
+  // half index is a compile-time constant in the index arithmetic
+  const int nbr = FF ? 2 : (a.split ? 2 : 1);
+#pragma unroll(FF ? 2 : 1)
+  for (int b = 0; b < nbr; ++b) {
+    if (b) cp_async_wait_all();       // phase table staged
+    __syncthreads();
+    float2 w[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) w[m] = b ? cmul(xr[m], phs[t + TT * m]) : xr[m];
+    fft_any<P, false>(w, t, spec, twr, tw);
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < R1; ++m) {
+      if constexpr (PD == TT) *spec.cyc(t, m) = w[m];
+      else spec.st(t + TT * m, w[m]);
+    }
+    cp_async_wait_all();              // this branch's symbol row
+    __syncthreads();
+    // row cc of the symbol multiply at the thread's frequencies
+    if constexpr (FF) {
+      // frequency f = 2l + b is stored directly for l < N/2 (m < R1/2) and
+      // folded to 2N - f, index N - l - b, with the fold signs for l >= N/2
+#pragma unroll
+      for (int m = 0; m < R1; ++m) {
+        const bool hi = m >= R1 / 2;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          const float2 sv = hi ? rowb[kr[j] + (N - b - t - TT * m)] : rowb[kr[j] + (t + TT * m)];
+          const float sgn = hi ? sgf1[j] : sgf0[j];
+          const SmLine<PD, TT> sj{lbase + j * CF::GS};
+          const float2 xv = (PD == TT) ? *sj.cyc(t, m) : sj.ld(t + TT * m);
+          // acc += sgn * (sv * xv): the parity sign rides on the accumulating FMA
+          const float px = fmaf(sv.x, xv.x, -sv.y * xv.y);
+          const float py = fmaf(sv.x, xv.y, sv.y * xv.x);
+          acc.x = fmaf(sgn, px, acc.x);
+          acc.y = fmaf(sgn, py, acc.y);
+        }
+        w[m] = acc;
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < R1; ++m) {
+        const int l = t + TT * m;
+        int f = a.split ? 2 * l + b : l;
+        unsigned sg = sg0;
+        if (S.compressed && f > nl) { f = 2 * nl - f; sg = sg1; }
+        const int pb = f & 1;
+        const int fi = f >> 1;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          float2 sv = __ldg(&Sd[off[pb][j] + fi]);
+          if ((sg >> j) & 1) { sv.x = -sv.x; sv.y = -sv.y; }
+          const SmLine<PD, TT> sj{lbase + j * CF::GS};
+          acc = cadd(acc, cmul(sv, sj.ld(l)));
+        }
+        w[m] = acc;
+      }
+    }
+    __syncthreads();
+    if (b == 0 && a.split) stage_row(1);   // overlaps the inverse and the odd forward transform
+    fft_any<P, true>(w, t, spec, twr, tw);
+    if (a.split && b == 0) {
+#pragma unroll
+      for (int m = 0; m < R1; ++m) stash[t + TT * m] = w[m];
+    } else {
+      float2* __restrict__ out = (float2*)nd.out + base;
+      if (ok) {
+#pragma unroll
+        for (int m = 0; m < R1; ++m) {
+          float2 y = w[m];
+          if (a.split) y = cadd(stash[t + TT * m], cmulc(y, phs[t + TT * m]));
+          out[TT * m] = y;
+        }
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+template <class P, int C, bool FF>
+static cudaError_t leaf_reg_pf(const LeafArgs& a, cudaStream_t st) {
+  typedef LeafCfg<P, C> CF;
+  const long long total = (long long)a.nrhs * a.lines;
+  const long long nt = (total + CF::LPC - 1) / CF::LPC;
+  if (nt <= 0 || a.nnodes <= 0) return cudaSuccess;
+  const size_t sm = CF::smem(FF ? a.sym.nsym : 0);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_leaf_cg<P, C, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr = true;
+  }
+  if (sm > 227 * 1024) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)nt, (unsigned)a.nnodes);
+  k_leaf_cg<P, C, FF><<<grid, CF::THREADS, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class P, int C>
+static cudaError_t leaf_reg_p(const LeafArgs& a, cudaStream_t st) {
+  const bool ff = a.split && a.sym.compressed && a.sym.n[a.dl] == a.N;
+  return ff ? leaf_reg_pf<P, C, true>(a, st) : leaf_reg_pf<P, C, false>(a, st);
+}
+
+bool leaf_reg_supported(const LeafArgs& a, size_t esz) {
+  if (esz != sizeof(float2)) return false;
+  if (!(a.c == 1 || a.c == 3)) return false;
+  return reg_length(a.N);
+}
+
+template <int C>
+static cudaError_t leaf_reg_c(const LeafArgs& a, cudaStream_t st) {
+  switch (a.N) {
+    case 24: return leaf_reg_p<RP24, C>(a, st);
+    case 48: return leaf_reg_p<RP48, C>(a, st);
+    case 60: return leaf_reg_p<RP60, C>(a, st);
+    case 96: return leaf_reg_p<RP96, C>(a, st);
+    case 192: return leaf_reg_p<RP192, C>(a, st);
+    case 32: return leaf_reg_p<RP32, C>(a, st);
+    case 64: return leaf_reg_p<RP64, C>(a, st);
+    case 128: return leaf_reg_p<RP128, C>(a, st);
+    case 256: return leaf_reg_p<RP256, C>(a, st);
+    case 512: return leaf_reg_p<RP512, C>(a, st);
+  }
+  return cudaErrorNotSupported;
+}
+
+cudaError_t launch_leaf_reg(const LeafArgs& a, cudaStream_t st) {
+  return a.c == 1 ? leaf_reg_c<1>(a, st) : leaf_reg_c<3>(a, st);
+}
+
+}  // namespace btmv

@@ -1,0 +1,114 @@
+// Register-resident strided line passes (forward split and merge) for the
+// line lengths fast.cuh provides plans for.
+#include "fast.cuh"
+
+namespace btmv {
+
+// ------------------------------------------------------------- strided pass
+// columns per tile: 16 x 8 B = 128 B rows (8 for N = 512 to stay in 32 KB)
+template <class P> __host__ __device__ constexpr int pass_cols() { return P::N <= 256 ? 16 : 8; }
+
+template <class P, int MODE>
+__global__ void __launch_bounds__(pass_cols<P>() * P::T) k_pass_reg(const PassArgs a) {
+  constexpr int R1 = P::R1, TT = P::T, N = P::N, PW = pass_cols<P>();
+  __shared__ float2 sm[N * PW];
+  const int col = threadIdx.x % PW;
+  const int t = threadIdx.x / PW;
+  const long long gl = (long long)blockIdx.x * PW + col;
+  const bool ok = gl < a.g.lines;
+  const long long inner = a.g.Itot;
+  const long long o = ok ? gl / inner : 0;
+  const long long ii = ok ? gl - o * inner : 0;
+  const long long base = o * (long long)N * inner + ii;   // same geometry for every array
+  const float2* __restrict__ tw = (const float2*)a.fft.tw;
+  const float2* __restrict__ ph = (const float2*)a.fft.ph;
+  const SmCol<PW, TT> smc{sm + col};
+  TwReg<P> twr;
+  if constexpr (P::R3 == 1) twr.load(t, tw);
+
+  if (MODE == 0) {
+    const float2* __restrict__ in = (const float2*)a.in0;
+    float2 v[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) v[m] = ok ? in[base + (long long)(t + TT * m) * inner] : make_float2(0.f, 0.f);
+    if (a.out0) {
+      float2 w[R1];
+#pragma unroll
+      for (int m = 0; m < R1; ++m) w[m] = v[m];
+      fft_any<P, false>(w, t, smc, twr, tw);
+      float2* __restrict__ out = (float2*)a.out0;
+      if (ok)
+#pragma unroll
+        for (int m = 0; m < R1; ++m) out[base + (long long)(t + TT * m) * inner] = w[m];
+    }
+    if (a.out1) {
+#pragma unroll
+      for (int m = 0; m < R1; ++m) v[m] = cmul(v[m], __ldg(&ph[t + TT * m]));
+      fft_any<P, false>(v, t, smc, twr, tw);
+      float2* __restrict__ out = (float2*)a.out1;
+      if (ok)
+#pragma unroll
+        for (int m = 0; m < R1; ++m) out[base + (long long)(t + TT * m) * inner] = v[m];
+    }
+  } else {
+    const float2* __restrict__ ine = (const float2*)a.in0;
+    const float2* __restrict__ ino = (const float2*)a.in1;
+    float2 e[R1], od[R1];
+#pragma unroll
+    for (int m = 0; m < R1; ++m) e[m] = ok ? ine[base + (long long)(t + TT * m) * inner] : make_float2(0.f, 0.f);
+    if (ino) {
+#pragma unroll
+      for (int m = 0; m < R1; ++m) od[m] = ok ? ino[base + (long long)(t + TT * m) * inner] : make_float2(0.f, 0.f);
+    }
+    fft_any<P, true>(e, t, smc, twr, tw);
+    if (ino) {
+      fft_any<P, true>(od, t, smc, twr, tw);
+#pragma unroll
+      for (int m = 0; m < R1; ++m) e[m] = cadd(e[m], cmulc(od[m], __ldg(&ph[t + TT * m])));
+    }
+    float2* __restrict__ out = (float2*)a.out0;
+    if (ok)
+#pragma unroll
+      for (int m = 0; m < R1; ++m) out[base + (long long)(t + TT * m) * inner] = e[m];
+  }
+}
+
+template <class P>
+static cudaError_t pass_reg_p(int mode, const PassArgs& a, cudaStream_t st) {
+  constexpr int PW = pass_cols<P>();
+  const long long nt = (a.g.lines + PW - 1) / PW;
+  if (nt <= 0) return cudaSuccess;
+  if (mode == 0) k_pass_reg<P, 0><<<(unsigned)nt, PW * P::T, 0, st>>>(a);
+  else           k_pass_reg<P, 1><<<(unsigned)nt, PW * P::T, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+bool pass_reg_supported(const PassArgs& a, size_t esz) {
+  if (esz != sizeof(float2)) return false;
+  if (a.g.contig || a.g.ni != 1) return false;
+  const int N = a.g.N;
+  if (!reg_length(N)) return false;
+  // plain contiguous node geometry: every array [outer][N][inner], full lines
+  const ArrMap* ms[4] = {&a.a_in0, &a.a_in1, &a.a_out0, &a.a_out1};
+  for (auto m : ms)
+    if (m->os != (long long)N * a.g.Itot || m->es != a.g.Itot || m->is[0] != 1 || m->len != N) return false;
+  return true;
+}
+
+cudaError_t launch_pass_reg(int mode, const PassArgs& a, cudaStream_t st) {
+  switch (a.g.N) {
+    case 24: return pass_reg_p<RP24>(mode, a, st);
+    case 48: return pass_reg_p<RP48>(mode, a, st);
+    case 60: return pass_reg_p<RP60>(mode, a, st);
+    case 96: return pass_reg_p<RP96>(mode, a, st);
+    case 192: return pass_reg_p<RP192>(mode, a, st);
+    case 32: return pass_reg_p<RP32>(mode, a, st);
+    case 64: return pass_reg_p<RP64>(mode, a, st);
+    case 128: return pass_reg_p<RP128>(mode, a, st);
+    case 256: return pass_reg_p<RP256>(mode, a, st);
+    case 512: return pass_reg_p<RP512>(mode, a, st);
+  }
+  return cudaErrorNotSupported;
+}
+
+}  // namespace btmv

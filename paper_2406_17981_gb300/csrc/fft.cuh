@@ -193,6 +193,65 @@ template <int RAD, bool INV, class T> __device__ __forceinline__ void dft_odd(T*
   for (int r = 0; r < RAD; ++r) a[r] = out[r];
 }
 
+// cos and sin of 2 pi e / R evaluated at compile time: the angle is reduced
+// to [-pi, pi] on the integer e, then summed by the Taylor series (20 terms,
+// truncation below 1e-20 on that interval).
+constexpr double kPiD = 3.141592653589793238462643383279502884;
+constexpr double ct_angle(int e, int R) {
+  e %= R;
+  if (2 * e > R) e -= R;
+  return 2.0 * kPiD * (double)e / (double)R;
+}
+constexpr double ct_sin2pi(int e, int R) {
+  const double x = ct_angle(e, R), x2 = x * x;
+  double term = x, sum = x;
+  for (int k = 1; k <= 20; ++k) { term = -term * x2 / ((2.0 * k) * (2.0 * k + 1.0)); sum += term; }
+  return sum;
+}
+constexpr double ct_cos2pi(int e, int R) {
+  const double x = ct_angle(e, R), x2 = x * x;
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k <= 20; ++k) { term = -term * x2 / ((2.0 * k - 1.0) * (2.0 * k)); sum += term; }
+  return sum;
+}
+
+template <int RAD, bool INV, class T> __device__ __forceinline__ void dft(T* a);
+
+// DFT of size P*Q from P-point and Q-point DFTs (Cooley-Tukey): with
+// n = Q n1 + n2 and k = k1 + P k2, inner DFT_P over n1, twiddle
+// w_{PQ}^{n2 k1} (compile-time constants), outer DFT_Q over n2.
+template <int P, int Q, bool INV, class T> __device__ __forceinline__ void dft_pq(T* a) {
+  typedef typename K<T>::r R;
+  constexpr int RR = P * Q;
+  T b[RR];
+#pragma unroll
+  for (int n2 = 0; n2 < Q; ++n2) {
+    T v[P];
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) v[n1] = a[Q * n1 + n2];
+    dft<P, INV>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      const int e = n2 * k1;
+      if (e == 0) {
+        b[n2 * P + k1] = v[k1];
+      } else {
+        const R c = (R)ct_cos2pi(e, RR), sn = (R)ct_sin2pi(e, RR);
+        b[n2 * P + k1] = twm<INV>(v[k1], mkc(c, -sn));
+      }
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) {
+    T u[Q];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) u[n2] = b[n2 * P + k1];
+    dft<Q, INV>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) a[k1 + P * k2] = u[k2];
+  }
+}
+
 template <int RAD, bool INV, class T> __device__ __forceinline__ void dft(T* a) {
   if constexpr (RAD == 2) dft2<INV>(a);
   else if constexpr (RAD == 3) dft3<INV>(a);
@@ -201,6 +260,11 @@ template <int RAD, bool INV, class T> __device__ __forceinline__ void dft(T* a) 
   else if constexpr (RAD == 7) dft_odd<7, INV>(a);
   else if constexpr (RAD == 8) dft8<INV>(a);
   else if constexpr (RAD == 16) dft16<INV>(a);
+  else if constexpr (RAD == 6) dft_pq<2, 3, INV>(a);
+  else if constexpr (RAD == 12) dft_pq<4, 3, INV>(a);
+  else if constexpr (RAD == 24) dft_pq<8, 3, INV>(a);
+  else if constexpr (RAD == 30) dft_pq<6, 5, INV>(a);
+  else static_assert(RAD == 2, "radix not provided");
 }
 
 // Quotient x / d for 0 <= x < 2^22 through a float reciprocal: with inv the

@@ -171,7 +171,8 @@ def test_errors_and_noop():
 
 
 REG_SIZES = [(32,), (64,), (128,), (256,), (512,), (32, 64), (8, 256), (512, 8), (64, 32, 128),
-             (16, 32, 64), (3, 128, 5), (128, 128, 16)]
+             (16, 32, 64), (3, 128, 5), (128, 128, 16),
+             (24,), (48,), (60,), (96,), (192,), (24, 48), (60, 12), (96, 24, 6), (12, 30, 48), (20, 192)]
 
 
 @pytest.mark.parametrize("n", REG_SIZES)
