@@ -37,6 +37,11 @@ typedef RP<48, 12, 4, 1> RP48;
 typedef RP<60, 30, 2, 1> RP60;
 typedef RP<96, 24, 4, 1> RP96;
 typedef RP<192, 24, 8, 1> RP192;
+// three-stage plans: T | N/R2, T | N/R3 and R3 | R1
+typedef RP<160, 20, 4, 2> RP160;
+typedef RP<320, 20, 4, 4> RP320;
+typedef RP<384, 24, 8, 2> RP384;
+typedef RP<768, 24, 4, 8> RP768;
 
 // shared-memory views of one line
 // Shared-memory views of one line.  ld/st take a point index p; cyc(t, m)
@@ -181,7 +186,8 @@ __device__ __forceinline__ void fft_any(float2 (&a)[P::R1], int t, const SM& sm,
 
 static inline bool reg_length(int N) {
   switch (N) {
-    case 24: case 32: case 48: case 60: case 64: case 96: case 128: case 192: case 256: case 512: return true;
+    case 24: case 32: case 48: case 60: case 64: case 96: case 128: case 160: case 192: case 256: case 320:
+    case 384: case 512: case 768: return true;
   }
   return false;
 }

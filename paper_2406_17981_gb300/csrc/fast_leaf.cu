@@ -256,6 +256,10 @@ static cudaError_t leaf_reg_c(const LeafArgs& a, cudaStream_t st) {
     case 60: return leaf_reg_p<RP60, C>(a, st);
     case 96: return leaf_reg_p<RP96, C>(a, st);
     case 192: return leaf_reg_p<RP192, C>(a, st);
+    case 160: return leaf_reg_p<RP160, C>(a, st);
+    case 320: return leaf_reg_p<RP320, C>(a, st);
+    case 384: return leaf_reg_p<RP384, C>(a, st);
+    case 768: return leaf_reg_p<RP768, C>(a, st);
     case 32: return leaf_reg_p<RP32, C>(a, st);
     case 64: return leaf_reg_p<RP64, C>(a, st);
     case 128: return leaf_reg_p<RP128, C>(a, st);

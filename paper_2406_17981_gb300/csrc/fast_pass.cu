@@ -102,6 +102,10 @@ cudaError_t launch_pass_reg(int mode, const PassArgs& a, cudaStream_t st) {
     case 60: return pass_reg_p<RP60>(mode, a, st);
     case 96: return pass_reg_p<RP96>(mode, a, st);
     case 192: return pass_reg_p<RP192>(mode, a, st);
+    case 160: return pass_reg_p<RP160>(mode, a, st);
+    case 320: return pass_reg_p<RP320>(mode, a, st);
+    case 384: return pass_reg_p<RP384>(mode, a, st);
+    case 768: return pass_reg_p<RP768>(mode, a, st);
     case 32: return pass_reg_p<RP32>(mode, a, st);
     case 64: return pass_reg_p<RP64>(mode, a, st);
     case 128: return pass_reg_p<RP128>(mode, a, st);
