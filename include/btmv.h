@@ -91,10 +91,16 @@ enum {
                                       line in one tile, each frequency's c x c
                                       symbol block read once for all of them
                                       (CUDA-core contraction)                  */
-  BTMV_FLAG_TENSOR_CORE = 1u << 3  /* as BTMV_FLAG_SHARED_RHS, with the c x c x
+  BTMV_FLAG_TENSOR_CORE = 1u << 3, /* as BTMV_FLAG_SHARED_RHS, with the c x c x
                                       nrhs contraction on tensor cores (c = 3,
                                       complex64, nrhs >= 2): TF32 mma with a
                                       high/low split, FP32 accumulation        */
+  BTMV_FLAG_TWO_STREAMS = 1u << 4  /* split, d >= 3: run the two top-level
+                                      subtrees of Algorithm 1 on two streams
+                                      (the caller's and a plan stream) so the
+                                      passes of one overlap the leaves of the
+                                      other; costs d-2 more workspace vectors
+                                      (peak d+1 -> 2d-1 vectors)              */
 };
 
 /*

@@ -127,9 +127,30 @@ static void free_plan(btmv_plan p) {
   p->tab.owner.reset();       // freed with the last plan sharing them
   p->sym_owner.reset();
   if (p->ws) cudaFree(p->ws);
+  if (p->ws2) cudaFree(p->ws2);
+  if (p->side) cudaStreamDestroy(p->side);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->stage_x) cudaFree(p->stage_x);
   if (p->stage_y) cudaFree(p->stage_y);
   delete p;
+}
+
+// BTMV_FLAG_TWO_STREAMS with d >= 3: a second set of d-2 workspace vectors
+// for the second top-level subtree, a plan stream and fork / join events.
+static btmv_status setup_two_streams(btmv_plan p, size_t V) {
+  if (!(p->flags & BTMV_FLAG_TWO_STREAMS) || p->algo != BTMV_ALGO_SPLIT || p->d < 3) return BTMV_OK;
+  const size_t n2 = (size_t)(p->d - 2);
+  cudaError_t e = cudaMalloc(&p->ws2, n2 * V);
+  if (e != cudaSuccess) return fail(BTMV_E_NOMEM, "plan: second-subtree workspace: %s", cudaGetErrorString(e));
+  p->ws_bytes += n2 * V;
+  p->W2.push_back(nullptr);                       // index m = 1..d-2 as in W
+  for (size_t i = 0; i < n2; ++i) p->W2.push_back((unsigned char*)p->ws2 + i * V);
+  if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return fail(BTMV_E_CUDA, "plan: side stream");
+  return BTMV_OK;
 }
 
 extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n, int c, int precision,
@@ -143,7 +164,8 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
   if (precision != BTMV_C64 && precision != BTMV_C128) return fail(BTMV_E_ARG, "plan_create: bad precision %d", precision);
   if (algo != BTMV_ALGO_SPLIT && algo != BTMV_ALGO_FULL) return fail(BTMV_E_ARG, "plan_create: bad algo %d", algo);
   if (max_rhs < 1) return fail(BTMV_E_ARG, "plan_create: max_rhs=%d < 1", max_rhs);
-  if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC | BTMV_FLAG_SHARED_RHS | BTMV_FLAG_TENSOR_CORE))
+  if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC | BTMV_FLAG_SHARED_RHS | BTMV_FLAG_TENSOR_CORE |
+                          BTMV_FLAG_TWO_STREAMS))
     return fail(BTMV_E_ARG, "plan_create: unknown flags 0x%x", flags);
   for (int m = 0; m < d; ++m) {
     if (n[m] < 1) return fail(BTMV_E_ARG, "plan_create: n[%d]=%d < 1", m, n[m]);
@@ -183,6 +205,8 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
     else
       p->W.push_back(p->ws);
   }
+  st = setup_two_streams(p, V);
+  if (st != BTMV_OK) { free_plan(p); return st; }
   *out = p;
   return BTMV_OK;
 }
@@ -192,7 +216,8 @@ extern "C" btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flag
   if (!src || !out) return fail(BTMV_E_ARG, "plan_clone: NULL argument");
   *out = nullptr;
   if (max_rhs < 1) return fail(BTMV_E_ARG, "plan_clone: max_rhs=%d < 1", max_rhs);
-  if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC | BTMV_FLAG_SHARED_RHS | BTMV_FLAG_TENSOR_CORE))
+  if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC | BTMV_FLAG_SHARED_RHS | BTMV_FLAG_TENSOR_CORE |
+                          BTMV_FLAG_TWO_STREAMS))
     return fail(BTMV_E_ARG, "plan_clone: unknown flags 0x%x", flags);
   btmv_plan p = new btmv_plan_s();
   p->d = src->d; p->c = src->c; p->prec = src->prec; p->algo = src->algo; p->max_rhs = max_rhs; p->flags = flags;
@@ -537,25 +562,28 @@ static btmv_status leaf_launch(btmv_plan p, int nrhs, int nn, const LeafNode* no
 // level m (transformed along dims 0..m-1) is split along dim m into itself
 // (even half) and W[m] (odd half); at the last split level both children go
 // to one leaf launch; merges run on the way back up.
-static void split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, std::vector<Step>& out);
+static void split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, std::vector<Step>& out,
+                           const std::vector<void*>& W);
 
-static void split_descend(btmv_plan p, int m, void* buf, int prefix, std::vector<Step>& out) {
-  void* Wm = p->W[m];
+static void split_descend(btmv_plan p, int m, void* buf, int prefix, std::vector<Step>& out,
+                          const std::vector<void*>& W) {
+  void* Wm = W[m];
   Step f = {0, m, buf, nullptr, buf, Wm, 0, {}};
   out.push_back(f);
-  split_children(p, m, buf, Wm, prefix, prefix | (1 << m), out);
+  split_children(p, m, buf, Wm, prefix, prefix | (1 << m), out, W);
   Step g = {1, m, buf, Wm, buf, nullptr, 0, {}};
   out.push_back(g);
 }
 
-static void split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, std::vector<Step>& out) {
+static void split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, std::vector<Step>& out,
+                           const std::vector<void*>& W) {
   if (m + 1 == p->d - 1) {
     Step l = {2, p->d - 1, nullptr, nullptr, nullptr, nullptr, 2, {{e, e, pe}, {o, o, po}}};
     out.push_back(l);
     return;
   }
-  split_descend(p, m + 1, e, pe, out);
-  split_descend(p, m + 1, o, po, out);
+  split_descend(p, m + 1, e, pe, out, W);
+  split_descend(p, m + 1, o, po, out, W);
 }
 
 void btmv::split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& out) {
@@ -567,20 +595,48 @@ void btmv::split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& o
   }
   Step f = {0, 0, x, nullptr, y, p->W[0], 0, {}};
   out.push_back(f);
-  split_children(p, 0, y, p->W[0], 0, 1, out);
+  split_children(p, 0, y, p->W[0], 0, 1, out, p->W);
   Step g = {1, 0, y, p->W[0], y, nullptr, 0, {}};
   out.push_back(g);
 }
 
 template <class T>
-static btmv_status split_apply(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
-  std::vector<Step> steps;
-  split_steps(p, x, y, steps);
+static btmv_status run_steps(btmv_plan p, const std::vector<Step>& steps, int nrhs, cudaStream_t st) {
   for (const Step& s : steps) {
     if (s.kind == 2) TRY(leaf_launch<T>(p, nrhs, s.nn, s.nodes, false, st));
     else             TRY(split_pass<T>(p, s, nrhs, st));
   }
   return BTMV_OK;
+}
+
+template <class T>
+static btmv_status split_apply(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
+  std::vector<Step> steps;
+  if (!p->side) {
+    split_steps(p, x, y, steps);
+    return run_steps<T>(p, steps, nrhs, st);
+  }
+  // two top-level subtrees on two streams: the even one on st with W, the
+  // odd one on the plan's side stream with its own workspace W2, so that the
+  // memory-bound passes of one overlap the compute-bound leaves of the other
+  Step f = {0, 0, x, nullptr, y, p->W[0], 0, {}};
+  TRY(split_pass<T>(p, f, nrhs, st));
+  CUDA_TRY(cudaEventRecord(p->ev_fork, st));
+  CUDA_TRY(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+  std::vector<Step> a, b;
+  if (p->d - 1 == 1) {
+    Step l = {2, 1, nullptr, nullptr, nullptr, nullptr, 2, {{y, y, 0}, {p->W[0], p->W[0], 1}}};
+    a.push_back(l);
+  } else {
+    split_descend(p, 1, y, 0, a, p->W);
+    split_descend(p, 1, p->W[0], 1, b, p->W2);
+  }
+  TRY(run_steps<T>(p, a, nrhs, st));
+  TRY(run_steps<T>(p, b, nrhs, p->side));
+  CUDA_TRY(cudaEventRecord(p->ev_join, p->side));
+  CUDA_TRY(cudaStreamWaitEvent(st, p->ev_join, 0));
+  Step g = {1, 0, y, p->W[0], y, nullptr, 0, {}};
+  return split_pass<T>(p, g, nrhs, st);
 }
 
 // Plain full embedding with own kernels: pad fused into the first forward

@@ -54,6 +54,12 @@ struct btmv_plan_s {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   std::vector<void*> W;     // split: d-1 vectors; full: Z
+  // two-stream schedule (BTMV_FLAG_TWO_STREAMS): workspace of the second
+  // top-level subtree, its stream and the fork / join events
+  void* ws2 = nullptr;
+  std::vector<void*> W2;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // host staging
   void* stage_x = nullptr;
   void* stage_y = nullptr;

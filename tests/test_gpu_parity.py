@@ -255,3 +255,23 @@ def test_multi_rhs_contraction_paths(n, r, flag):
     assert rel(y, ref) <= 1e-5
     y0 = run_btmv(t_orth, x, n, c, 0, 0, flags_s, par)
     assert rel(y, y0) <= 2e-6
+
+
+@pytest.mark.parametrize("n", [(16, 12, 20), (128, 64, 32), (6, 8, 10, 12)])
+def test_two_stream_schedule(n):
+    """The two top-level subtrees on two streams give the one-stream result."""
+    c = 3 if len(n) == 3 else 1
+    t = W.random_generator(n, c, seed=19)
+    x = W.random_vector(n, c, seed=20, nrhs=2)
+    plan = bt.Plan(n, c, 0, max_rhs=2, flags=bt.BTMV_FLAG_TWO_STREAMS)
+    plan.set_kernel(t)
+    assert plan.info["workspace_bytes"] == (2 * len(n) - 3) * plan.info["vector_bytes"] * 2
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    yd = torch.zeros_like(xd)
+    for _ in range(2):
+        plan.apply(xd, yd, 2)
+    torch.cuda.synchronize()
+    plan.close()
+    y = yd.cpu().numpy().astype(np.complex128)
+    assert rel(y, OE.embed_matvec(t, round_input(x, 0))) <= 1e-5
+    assert rel(y, run_btmv(t, x, n, c, 0, 0)) <= 1e-6
