@@ -349,6 +349,7 @@ def main():
                                                                 np.linalg.norm(vals[:, 0]))
         extra["peak_hbm_split_bytes"] = info["symbol_bytes"] + info["workspace_bytes"] + info["table_bytes"] + 2 * V
         if not args.no_compare:
+            extra["two_stream_variant"] = time_two_streams(args, cfg, t, par, sflags, xc, prec, V)
             extra.update(compare_full(args, cfg, t, par, sflags, xc, prec, cdt, V, esz, info))
             full = extra["full_embedding_own"]
             extra["speedup_split_vs_full_own"] = full["ms_per_step"] / (ms_max / args.steps)
@@ -586,6 +587,39 @@ def run_serving(args):
             "speedup_vs_one_at_a_time_full": res["matvecs_per_s"] / base["matvecs_per_s"],
             "clocks": clocks}
     print(json.dumps(line))
+
+
+def time_two_streams(args, cfg, t, par, sflags, xc, prec, V):
+    """The same split apply with the two top-level subtrees on two streams
+    (BTMV_FLAG_TWO_STREAMS): faster when passes and leaves overlap, at the
+    cost of d-2 more workspace vectors."""
+    import torch
+
+    from paper_2406_17981_gb300 import btmv as bt
+    n, c = cfg["n"], cfg["c"]
+    if len(n) < 3:
+        return None
+    p = bt.Plan(n, c, prec, bt.BTMV_ALGO_SPLIT, max_rhs=1, flags=bt.BTMV_FLAG_TWO_STREAMS)
+    p.set_kernel(t, sflags, par)
+    info = p.info
+    npool = max(2, math.ceil(2 * L2_BYTES / (2 * V)) + 1)
+    xs = [torch.from_numpy(xc).cuda() for _ in range(npool)]
+    ys = [torch.empty_like(xs[0]) for _ in range(npool)]
+    steps = max(10, min(args.steps, 500))
+    for i in range(5):
+        p.apply(xs[i % npool], ys[i % npool], 1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(steps):
+        p.apply(xs[i % npool], ys[i % npool], 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    p.close()
+    return {"matvecs_per_s": 1000.0 / ms, "ms_per_step": ms,
+            "peak_hbm_bytes": info["symbol_bytes"] + info["workspace_bytes"] + info["table_bytes"] + 2 * V}
 
 
 def compare_full(args, cfg, t, par, sflags, xc, prec, cdt, V, esz, info_split):

@@ -5,6 +5,13 @@
 namespace btmv {
 
 // ------------------------------------------------------------- strided pass
+template <class P, bool INV, int MODE, class SM>
+__device__ __forceinline__ void fft_pass(float2 (&a)[P::R1], int t, const SM& sm, const TwReg<P>& twr,
+                                         const float2* __restrict__ tw) {
+  if constexpr (MODE == 1) fft_any<P, INV>(a, t, sm, twr, tw);
+  else fft_reg<P, INV>(a, t, sm, tw);
+}
+
 // columns per tile: 16 x 8 B = 128 B rows (8 for N = 512 to stay in 32 KB)
 template <class P> __host__ __device__ constexpr int pass_cols() { return P::N <= 256 ? 16 : 8; }
 
@@ -23,8 +30,10 @@ __global__ void __launch_bounds__(pass_cols<P>() * P::T) k_pass_reg(const PassAr
   const float2* __restrict__ tw = (const float2*)a.fft.tw;
   const float2* __restrict__ ph = (const float2*)a.fft.ph;
   const SmCol<PW, TT> smc{sm + col};
+  // register twiddles pay off in the merge pass (two transforms per thread);
+  // the forward pass keeps them in the L1-resident table (fewer registers)
   TwReg<P> twr;
-  if constexpr (P::R3 == 1) twr.load(t, tw);
+  if constexpr (P::R3 == 1 && MODE == 1) twr.load(t, tw);
 
   if (MODE == 0) {
     const float2* __restrict__ in = (const float2*)a.in0;
@@ -35,7 +44,7 @@ __global__ void __launch_bounds__(pass_cols<P>() * P::T) k_pass_reg(const PassAr
       float2 w[R1];
 #pragma unroll
       for (int m = 0; m < R1; ++m) w[m] = v[m];
-      fft_any<P, false>(w, t, smc, twr, tw);
+      fft_pass<P, false, MODE>(w, t, smc, twr, tw);
       float2* __restrict__ out = (float2*)a.out0;
       if (ok)
 #pragma unroll
@@ -44,7 +53,7 @@ __global__ void __launch_bounds__(pass_cols<P>() * P::T) k_pass_reg(const PassAr
     if (a.out1) {
 #pragma unroll
       for (int m = 0; m < R1; ++m) v[m] = cmul(v[m], __ldg(&ph[t + TT * m]));
-      fft_any<P, false>(v, t, smc, twr, tw);
+      fft_pass<P, false, MODE>(v, t, smc, twr, tw);
       float2* __restrict__ out = (float2*)a.out1;
       if (ok)
 #pragma unroll
