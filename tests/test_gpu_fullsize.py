@@ -1,0 +1,70 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py
+times: 128^3 c=3 Green (complex64) against the full FP64 oracle, 256^3 Green
+and skew against the direct sum at sampled output points (the definition,
+evaluated point by point), plus the skew identity x^T T x = 0 at full size."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import embed as OE
+from oracle import toeplitz as OT
+from tests.gpu_util import rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+bt = pytest.importorskip("paper_2406_17981_gb300.btmv")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    bt.lib()
+
+
+def _apply(n, t, par, flags_sym, x, plan_flags=0):
+    plan = bt.Plan(n, 3, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=1, flags=plan_flags)
+    plan.set_kernel(t, flags_sym, par)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros_like(xd)
+    plan.apply(xd, yd, 1)
+    torch.cuda.synchronize()
+    plan.close()
+    return yd.cpu().numpy().astype(np.complex128)
+
+
+@pytest.mark.parametrize("plan_flags", [0, bt.BTMV_FLAG_TWO_STREAMS])
+def test_128_cubed_green_against_full_oracle(plan_flags):
+    cfg = W.WORKLOADS["d3_128_c3_green_c64"]
+    n = cfg["n"]
+    t, par = W.green_dyadic_orthant(n, kh=cfg["kh"])
+    x = W.random_vector(n, 3, seed=cfg["x_seed"]).astype(np.complex64)
+    y = _apply(n, t, par, 3, x, plan_flags)
+    ref = OE.embed_matvec(W.orthant_to_full(t, par), x.astype(np.complex128),
+                          workers=len(os.sched_getaffinity(0)))
+    assert rel(y, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["d3_256_c3_green_c64", "d3_256_c3_skew_c64"])
+def test_256_cubed_sampled_direct_sum(name):
+    cfg = W.WORKLOADS[name]
+    n = cfg["n"]
+    if cfg["kind"] == "green":
+        t, par = W.green_dyadic_orthant(n, kh=cfg["kh"])
+    else:
+        t, par = W.skew_orthant(n, seed=cfg["t_seed"])
+    x = W.random_vector(n, 3, seed=cfg["x_seed"]).astype(np.complex64)
+    y = _apply(n, t, par, 3, x)
+    rng = np.random.default_rng(41)
+    pts = [tuple(int(v) for v in rng.integers(0, n)) for _ in range(12)]
+    pts += [(0, 0, 0), (255, 255, 255), (0, 255, 128)]            # corners and a face
+    ref = OT.direct_points(W.orthant_to_full(t, par), x.astype(np.complex128), pts)[:, 0]
+    got = np.stack([y[(0, slice(None)) + p] for p in pts])
+    assert rel(got, ref) <= 1e-5
+    if cfg["kind"] == "skew":
+        xr = x.astype(np.complex128)
+        assert abs(np.sum(xr * y)) <= 1e-5 * np.linalg.norm(xr) * np.linalg.norm(y)
