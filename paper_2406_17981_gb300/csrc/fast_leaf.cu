@@ -53,52 +53,76 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
   float2* const stash = gbuf + CF::SPN;
   float2* const phs = smem_cg + CF::LPC * C * CF::GS;           // phase table P (N values)
   const SymDev& S = a.sym;
-  float2* const rowb = phs + N + li * CF::line_stride(S.nsym);    // staged symbol row of this line
+  constexpr int NS = C == 3 ? 6 : 1;                            // stored blocks staged by FF kernels
+  float2* const rowb = phs + N + li * CF::line_stride(FF ? NS : 0);  // staged symbol row of this line
   const LeafNode nd = a.nodes[blockIdx.y];
-  const long long gline = (long long)blockIdx.x * CF::LPC + li;   // over (rhs, line)
-  const bool ok = gline < (long long)a.nrhs * a.lines;
-  const long long q = ok ? gline / a.lines : 0;
-  const long long line = ok ? gline - q * a.lines : 0;
-  const long long base = q * a.rhs_stride + cc * a.comp_stride + line * N + t;
+  // 32-bit line arithmetic: the launcher guarantees nrhs * lines < 2^31
+  const unsigned lines = (unsigned)a.lines;
+  const unsigned gline = blockIdx.x * (unsigned)CF::LPC + (unsigned)li;   // over (rhs, line)
+  const bool ok = gline < (unsigned)a.nrhs * lines;
+  const unsigned q = ok ? gline / lines : 0u;
+  const unsigned line = ok ? gline - q * lines : 0u;
+  const long long base = (long long)q * a.rhs_stride + cc * a.comp_stride + (long long)line * N + t;
   const float2* __restrict__ tw = (const float2*)a.fft.tw;
   const float2* __restrict__ ph = (const float2*)a.fft.ph;
 
-  // symbol addressing for this line
+  // symbol addressing for this line: split-grid frequency of each line dim,
+  // its parity class and (compressed store) the fold to 2n - f
   const int dl = a.dl;
   int clsp = 0, foldp = 0;
-  long long lin = 0;
+  unsigned lin = 0;
   {
-    int fpre[MAX_D];
-    long long r = line;
-    for (int m = dl - 1; m >= 0; --m) {
-      const int im = (int)(r % a.ext[m]);
-      r /= a.ext[m];
-      fpre[m] = a.split ? 2 * im + ((nd.prefix >> m) & 1) : im;
+    int fpre[MAX_D - 1];
+    unsigned r = line;
+#pragma unroll
+    for (int m = MAX_D - 2; m >= 1; --m) {
+      if (m < dl) {
+        const unsigned e = (unsigned)a.ext[m];
+        const unsigned r2 = r / e;
+        fpre[m] = (int)(r - r2 * e);
+        r = r2;
+      }
     }
-    for (int m = 0; m < dl; ++m) clsp = (clsp << 1) | (fpre[m] & 1);
-    for (int m = 0; m < dl; ++m) {
-      int fm = fpre[m];
-      if (S.compressed && fm > S.n[m]) { fm = 2 * S.n[m] - fm; foldp |= 1 << m; }
-      lin = lin * S.J[clsp << 1][m] + (fm >> 1);
-    }
+    fpre[0] = (int)r;
+#pragma unroll
+    for (int m = 0; m < MAX_D - 1; ++m)
+      if (m < dl) {
+        fpre[m] = a.split ? 2 * fpre[m] + ((nd.prefix >> m) & 1) : fpre[m];
+        clsp = (clsp << 1) | (fpre[m] & 1);
+      }
+#pragma unroll
+    for (int m = 0; m < MAX_D - 1; ++m)
+      if (m < dl) {
+        int fm = fpre[m];
+        if (S.compressed && fm > S.n[m]) { fm = 2 * S.n[m] - fm; foldp |= 1 << m; }
+        lin = lin * (unsigned)S.J[clsp << 1][m] + (unsigned)(fm >> 1);
+      }
   }
   const int nl = S.n[dl];
   const float2* __restrict__ Sd = (const float2*)S.data;
-  // FF: split leaf on the mirror-compressed store with n_d == N; the line's
-  // row of each parity class is staged in shared memory while the
-  // transforms run
-  const int nsym = S.nsym;
+  // FF: split leaf on the mirror-compressed store with n_d == N and NS
+  // stored blocks (block-symmetric c = 3, or c = 1); the line's row of each
+  // parity class is staged in shared memory while the transforms run
+  const int nsym = FF ? NS : S.nsym;
   // bank-half shift of each stored block of the c = 3 block-symmetric row:
   // blocks 00 11 22 01 02 12 -> 0 0 0 1 0 1
   auto row_pos = [&](int k) { return k * JP + ((C == 3 && nsym == 6 && (k == 3 || k == 5)) ? 8 : 0); };
   auto stage_row = [&](int bb) {
-    if (!FF || !ok) return;
-    const int cl = (clsp << 1) | bb;
-    const int J = S.J[cl][dl];
-    const float2* src = Sd + S.cls_off[cl] + lin * J;
-    const long long blk = S.blk[cl];
-    for (int k = 0; k < nsym; ++k)
-      for (int j = lt; j < J; j += C * TT) cp_async8(rowb + row_pos(k) + j, src + k * blk + j);
+    if constexpr (FF) {
+      if (!ok) return;
+      const int cl = (clsp << 1) | bb;
+      const int J = S.J[cl][dl];
+      const float2* src = Sd + S.cls_off[cl] + (long long)lin * J;
+      const long long blk = S.blk[cl];
+      constexpr int IT = (N / 2 + 1 + C * TT - 1) / (C * TT);
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+          const int j = lt + i * C * TT;
+          if (j < J) cp_async8(rowb + row_pos(k) + j, src + k * blk + j);
+        }
+    }
   };
   for (int e = threadIdx.x; e < N; e += CF::THREADS) cp_async8(phs + e, ph + e);
   stage_row(0);
@@ -106,12 +130,9 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
   TwReg<P> twr;
   if constexpr (P::R3 == 1) twr.load(t, tw);
 
-  float2 xr[R1];
-  {
-    const float2* __restrict__ in = (const float2*)nd.in + base;
-#pragma unroll
-    for (int m = 0; m < R1; ++m) xr[m] = ok ? in[TT * m] : make_float2(0.f, 0.f);
-  }
+  // the input line is read once per half (the odd half's read hits in cache)
+  // rather than held in registers across both halves
+  const float2* __restrict__ xin = (const float2*)nd.in + base;
 
   long long off[2][C];
   int kr[C];
@@ -123,7 +144,7 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
 #pragma unroll
     for (int bb = 0; bb < 2; ++bb) {
       const int cl = (clsp << 1) | bb;
-      off[bb][j] = S.cls_off[cl] + lin * S.J[cl][dl] + (long long)k * S.blk[cl];
+      off[bb][j] = S.cls_off[cl] + (long long)lin * S.J[cl][dl] + (long long)k * S.blk[cl];
     }
     sg0 |= (unsigned)(__popc(S.oddmask[k] & foldp) & 1) << j;
     sg1 |= (unsigned)(__popc(S.oddmask[k] & (foldp | (1 << dl))) & 1) << j;
@@ -136,16 +157,19 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
   }
   float2* const lbase = smem_cg + (li * C) * CF::GS;   // spectra of this line's groups
 
-  // FF kernels always run both halves (split leaves); unrolled so that the
-  // half index is a compile-time constant in the index arithmetic
+  // split leaves run both halves; the loop stays rolled (half the code of
+  // the unrolled form, which measured slower)
   const int nbr = FF ? 2 : (a.split ? 2 : 1);
-#pragma unroll(FF ? 2 : 1)
+#pragma unroll 1
   for (int b = 0; b < nbr; ++b) {
     if (b) cp_async_wait_all();       // phase table staged
     __syncthreads();
     float2 w[R1];
 #pragma unroll
-    for (int m = 0; m < R1; ++m) w[m] = b ? cmul(xr[m], phs[t + TT * m]) : xr[m];
+    for (int m = 0; m < R1; ++m) {
+      const float2 xv0 = ok ? xin[TT * m] : make_float2(0.f, 0.f);
+      w[m] = b ? cmul(xv0, phs[t + TT * m]) : xv0;
+    }
     fft_any<P, false>(w, t, spec, twr, tw);
     __syncwarp();
 #pragma unroll
@@ -238,13 +262,14 @@ static cudaError_t leaf_reg_pf(const LeafArgs& a, cudaStream_t st) {
 
 template <class P, int C>
 static cudaError_t leaf_reg_p(const LeafArgs& a, cudaStream_t st) {
-  const bool ff = a.split && a.sym.compressed && a.sym.n[a.dl] == a.N;
+  const bool ff = a.split && a.sym.compressed && a.sym.n[a.dl] == a.N && a.sym.nsym == (C == 3 ? 6 : 1);
   return ff ? leaf_reg_pf<P, C, true>(a, st) : leaf_reg_pf<P, C, false>(a, st);
 }
 
 bool leaf_reg_supported(const LeafArgs& a, size_t esz) {
   if (esz != sizeof(float2)) return false;
   if (!(a.c == 1 || a.c == 3)) return false;
+  if ((long long)a.nrhs * a.lines >= (1ll << 31)) return false;   // 32-bit line indices
   return reg_length(a.N);
 }
 
