@@ -5,80 +5,82 @@
 namespace btmv {
 
 // ------------------------------------------------------------- strided pass
-template <class P, bool INV, int MODE, class SM>
-__device__ __forceinline__ void fft_pass(float2 (&a)[P::R1], int t, const SM& sm, const TwReg<P>& twr,
-                                         const float2* __restrict__ tw) {
-  if constexpr (MODE == 1) fft_any<P, INV>(a, t, sm, twr, tw);
-  else fft_reg<P, INV>(a, t, sm, tw);
-}
-
 // columns per tile: 16 x 8 B = 128 B rows (8 for N = 512 to stay in 32 KB)
 template <class P> __host__ __device__ constexpr int pass_cols() { return P::N <= 256 ? 16 : 8; }
 
+// minimum resident blocks per SM for the radix-16 plans of 128..512 points,
+// scaled to 128-thread blocks: 6 for the forward split (80 registers), 4 for
+// the merge (two transforms in flight).  Both passes read the stage twiddles
+// from the L1-resident table (measured faster than register twiddles at
+// these occupancies).  The composite-radix plans hold more values per thread
+// and run unbounded.
+template <class P, int MODE> __host__ __device__ constexpr int pass_minb() {
+  constexpr int b = (MODE == 0 ? 6 : 4) * 128 / (pass_cols<P>() * P::T);
+  return (P::R1 == 16 && P::N >= 128 && b > 0) ? b : 1;
+}
 template <class P, int MODE>
-__global__ void __launch_bounds__(pass_cols<P>() * P::T) k_pass_reg(const PassArgs a) {
+__global__ void __launch_bounds__(pass_cols<P>() * P::T, pass_minb<P, MODE>()) k_pass_reg(const PassArgs a) {
   constexpr int R1 = P::R1, TT = P::T, N = P::N, PW = pass_cols<P>();
   __shared__ float2 sm[N * PW];
   const int col = threadIdx.x % PW;
   const int t = threadIdx.x / PW;
-  const long long gl = (long long)blockIdx.x * PW + col;
-  const bool ok = gl < a.g.lines;
-  const long long inner = a.g.Itot;
-  const long long o = ok ? gl / inner : 0;
-  const long long ii = ok ? gl - o * inner : 0;
-  const long long base = o * (long long)N * inner + ii;   // same geometry for every array
+  // 32-bit line arithmetic (the launcher guarantees lines < 2^31)
+  const unsigned gl = blockIdx.x * (unsigned)PW + (unsigned)col;
+  const bool ok = gl < (unsigned)a.g.lines;
+  const unsigned inner = (unsigned)a.g.Itot;
+  const unsigned o = ok ? gl / inner : 0u;
+  const unsigned ii = ok ? gl - o * inner : 0u;
+  // point t + T m of this line, the same geometry for every array
+  const long long base = ((long long)o * N + t) * inner + ii;
+  const long long step = (long long)TT * inner;
   const float2* __restrict__ tw = (const float2*)a.fft.tw;
   const float2* __restrict__ ph = (const float2*)a.fft.ph;
   const SmCol<PW, TT> smc{sm + col};
-  // register twiddles pay off in the merge pass (two transforms per thread);
-  // the forward pass keeps them in the L1-resident table (fewer registers)
-  TwReg<P> twr;
-  if constexpr (P::R3 == 1 && MODE == 1) twr.load(t, tw);
 
   if (MODE == 0) {
     const float2* __restrict__ in = (const float2*)a.in0;
     float2 v[R1];
 #pragma unroll
-    for (int m = 0; m < R1; ++m) v[m] = ok ? in[base + (long long)(t + TT * m) * inner] : make_float2(0.f, 0.f);
+    for (int m = 0; m < R1; ++m) v[m] = ok ? in[base + m * step] : make_float2(0.f, 0.f);
     if (a.out0) {
       float2 w[R1];
 #pragma unroll
       for (int m = 0; m < R1; ++m) w[m] = v[m];
-      fft_pass<P, false, MODE>(w, t, smc, twr, tw);
+      fft_reg<P, false>(w, t, smc, tw);
       float2* __restrict__ out = (float2*)a.out0;
       if (ok)
 #pragma unroll
-        for (int m = 0; m < R1; ++m) out[base + (long long)(t + TT * m) * inner] = w[m];
+        for (int m = 0; m < R1; ++m) out[base + m * step] = w[m];
     }
     if (a.out1) {
 #pragma unroll
       for (int m = 0; m < R1; ++m) v[m] = cmul(v[m], __ldg(&ph[t + TT * m]));
-      fft_pass<P, false, MODE>(v, t, smc, twr, tw);
+      fft_reg<P, false>(v, t, smc, tw);
       float2* __restrict__ out = (float2*)a.out1;
       if (ok)
 #pragma unroll
-        for (int m = 0; m < R1; ++m) out[base + (long long)(t + TT * m) * inner] = v[m];
+        for (int m = 0; m < R1; ++m) out[base + m * step] = v[m];
     }
   } else {
     const float2* __restrict__ ine = (const float2*)a.in0;
     const float2* __restrict__ ino = (const float2*)a.in1;
     float2 e[R1], od[R1];
 #pragma unroll
-    for (int m = 0; m < R1; ++m) e[m] = ok ? ine[base + (long long)(t + TT * m) * inner] : make_float2(0.f, 0.f);
+    for (int m = 0; m < R1; ++m) e[m] = ok ? ine[base + m * step] : make_float2(0.f, 0.f);
     if (ino) {
 #pragma unroll
-      for (int m = 0; m < R1; ++m) od[m] = ok ? ino[base + (long long)(t + TT * m) * inner] : make_float2(0.f, 0.f);
+      for (int m = 0; m < R1; ++m) od[m] = ok ? ino[base + m * step] : make_float2(0.f, 0.f);
     }
-    fft_any<P, true>(e, t, smc, twr, tw);
+    fft_reg<P, true>(e, t, smc, tw);
     if (ino) {
-      fft_any<P, true>(od, t, smc, twr, tw);
+      fft_reg<P, true>(od, t, smc, tw);
 #pragma unroll
       for (int m = 0; m < R1; ++m) e[m] = cadd(e[m], cmulc(od[m], __ldg(&ph[t + TT * m])));
     }
     float2* __restrict__ out = (float2*)a.out0;
     if (ok)
 #pragma unroll
-      for (int m = 0; m < R1; ++m) out[base + (long long)(t + TT * m) * inner] = e[m];
+      for (int m = 0; m < R1; ++m) out[base + m * step] = e[m];
   }
 }
 
@@ -97,6 +99,7 @@ bool pass_reg_supported(const PassArgs& a, size_t esz) {
   if (a.g.contig || a.g.ni != 1) return false;
   const int N = a.g.N;
   if (!reg_length(N)) return false;
+  if (a.g.lines >= (1ll << 31)) return false;                     // 32-bit line indices
   // plain contiguous node geometry: every array [outer][N][inner], full lines
   const ArrMap* ms[4] = {&a.a_in0, &a.a_in1, &a.a_out0, &a.a_out1};
   for (auto m : ms)
