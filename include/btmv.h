@@ -232,10 +232,11 @@ BTMV_API btmv_status btmv_apply_host_noalloc(btmv_plan p, const void* x, void* y
 /*
  * btmv_batch_tuning -- report the tuning chosen for a batch that has run:
  * cfg_out[0..7] = strided-pass tile lines, leaf lines per tile, leaf
- * right-hand sides per tile, radix order (0: 16 first, 1: 8 first), stages,
- * work items, blocks of the persistent launch, execution mode (0: one
- * persistent kernel, 1: one graph whose parallel branches run each problem's
- * own launches).  Arguments as for the
+ * right-hand sides per tile, radix order (0: 16 first, 1: 8 first), stages
+ * of the persistent launch (mode 1: kernel launches per graph replay), work
+ * items, blocks of the persistent launch, execution mode (0: one persistent
+ * kernel, 1: one graph whose parallel branches run each problem's own
+ * launches).  Arguments as for the
  * btmv_apply_batched call.  Errors: BTMV_E_ARG, BTMV_E_STATE (no such batch).
  */
 BTMV_API btmv_status btmv_batch_tuning(int count, const btmv_plan* plans, const void* const* x,

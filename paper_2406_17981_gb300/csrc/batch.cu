@@ -73,6 +73,7 @@ struct Entry {
   bool launched = false;
   unsigned long long lru = 0;
   int cfg_mode = 0;                   // mode of the stage table / graph in place
+  int kernels = 0;                    // kernel nodes of the captured graph
   void* h_err_dev() const { return &((BatchCtl*)d_ctl)->error; }
 };
 
@@ -331,6 +332,16 @@ btmv_status capture(Entry& e, cudaStream_t user) {
   cudaStreamDestroy(cs);
   if (s != BTMV_OK) { if (g) cudaGraphDestroy(g); return s; }
   if (ce != cudaSuccess) return fail(BTMV_E_CUDA, "apply_batched: end capture: %s", cudaGetErrorString(ce));
+  size_t nn = 0;
+  e.kernels = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++e.kernels;
+      }
+  }
   ce = cudaGraphInstantiate(&e.exec, g, 0);
   cudaGraphDestroy(g);
   if (ce != cudaSuccess) return fail(BTMV_E_CUDA, "apply_batched: instantiate: %s", cudaGetErrorString(ce));
@@ -486,7 +497,7 @@ extern "C" BTMV_API btmv_status btmv_batch_tuning(int count, const btmv_plan* pl
   if (!e) return fail(BTMV_E_STATE, "batch_tuning: no batch with these arguments has run");
   cfg_out[7] = e->cfg.mode;
   cfg_out[0] = e->cfg.TL; cfg_out[1] = e->cfg.Lt; cfg_out[2] = e->cfg.rq; cfg_out[3] = e->cfg.radix;
-  cfg_out[4] = e->nstages; cfg_out[5] = (int)std::min<long long>(e->nitems, 0x7fffffff); cfg_out[6] = e->grid;
+  cfg_out[4] = e->cfg.mode == 1 ? e->kernels : e->nstages; cfg_out[5] = (int)std::min<long long>(e->nitems, 0x7fffffff); cfg_out[6] = e->grid;
   return BTMV_OK;
 }
 

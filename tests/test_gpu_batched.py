@@ -183,8 +183,8 @@ def test_each_batched_execution_mode(mode, monkeypatch):
         if mode != "direct":
             cfg = bt.btmv_batch_tuning([p.handle for p in plans], xs, ys, [x.shape[0] for x in xs])
             assert cfg["mode"] == (0 if mode == "persistent" else 1)
-            if mode == "persistent":
-                assert cfg["stages"] == 8 * len(insts)
+            # persistent: 8 stages per d = 3 problem; branches: its 8 kernel launches
+            assert cfg["stages"] == 8 * len(insts)
     finally:
         for p in plans:
             p.close()
