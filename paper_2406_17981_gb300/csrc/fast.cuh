@@ -37,6 +37,7 @@ typedef RP<48, 12, 4, 1> RP48;
 typedef RP<60, 30, 2, 1> RP60;
 typedef RP<96, 24, 4, 1> RP96;
 typedef RP<192, 24, 8, 1> RP192;
+typedef RP<84, 42, 2, 1> RP84;
 // three-stage plans: T | N/R2, T | N/R3 and R3 | R1
 typedef RP<160, 20, 4, 2> RP160;
 typedef RP<320, 20, 4, 4> RP320;
@@ -186,7 +187,7 @@ __device__ __forceinline__ void fft_any(float2 (&a)[P::R1], int t, const SM& sm,
 
 static inline bool reg_length(int N) {
   switch (N) {
-    case 24: case 32: case 48: case 60: case 64: case 96: case 128: case 160: case 192: case 256: case 320:
+    case 24: case 32: case 48: case 60: case 64: case 84: case 96: case 128: case 160: case 192: case 256: case 320:
     case 384: case 512: case 768: return true;
   }
   return false;

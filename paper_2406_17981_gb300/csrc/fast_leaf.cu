@@ -134,28 +134,41 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
   // rather than held in registers across both halves
   const float2* __restrict__ xin = (const float2*)nd.in + base;
 
+  // OWN: the group's own spectrum is taken from registers.  Row cc is then
+  // walked in the order cc, cc+1, ... (mod C).  With T < 16 two groups of
+  // different components share a half-warp and the walk in the plain order
+  // 0..C-1 keeps their shared-memory reads conflict-free (the same
+  // spectrum, or buffers in opposite bank halves) and as few wavefronts, so
+  // OWN is used when a group fills its half-warps (T >= 16) or c = 1.
+  constexpr bool OWN = TT >= 16 || C == 1;
+  int jo[C];
+#pragma unroll
+  for (int jj = 0; jj < C; ++jj) jo[jj] = !OWN ? jj : cc + jj < C ? cc + jj : cc + jj - C;
   long long off[2][C];
   int kr[C];
   unsigned sg0 = 0, sg1 = 0;      // sign bits of row cc without / with a fold of the last dim
 #pragma unroll
-  for (int j = 0; j < C; ++j) {
-    const int k = S.comp[cc][j];
-    kr[j] = row_pos(k);
+  for (int jj = 0; jj < C; ++jj) {
+    const int k = S.comp[cc][jo[jj]];
+    kr[jj] = row_pos(k);
 #pragma unroll
     for (int bb = 0; bb < 2; ++bb) {
       const int cl = (clsp << 1) | bb;
-      off[bb][j] = S.cls_off[cl] + (long long)lin * S.J[cl][dl] + (long long)k * S.blk[cl];
+      off[bb][jj] = S.cls_off[cl] + (long long)lin * S.J[cl][dl] + (long long)k * S.blk[cl];
     }
-    sg0 |= (unsigned)(__popc(S.oddmask[k] & foldp) & 1) << j;
-    sg1 |= (unsigned)(__popc(S.oddmask[k] & (foldp | (1 << dl))) & 1) << j;
+    sg0 |= (unsigned)(__popc(S.oddmask[k] & foldp) & 1) << jj;
+    sg1 |= (unsigned)(__popc(S.oddmask[k] & (foldp | (1 << dl))) & 1) << jj;
   }
   float sgf0[C], sgf1[C];
 #pragma unroll
-  for (int j = 0; j < C; ++j) {
-    sgf0[j] = ((sg0 >> j) & 1) ? -1.f : 1.f;
-    sgf1[j] = ((sg1 >> j) & 1) ? -1.f : 1.f;
+  for (int jj = 0; jj < C; ++jj) {
+    sgf0[jj] = ((sg0 >> jj) & 1) ? -1.f : 1.f;
+    sgf1[jj] = ((sg1 >> jj) & 1) ? -1.f : 1.f;
   }
   float2* const lbase = smem_cg + (li * C) * CF::GS;   // spectra of this line's groups
+  float2* sp[C];
+#pragma unroll
+  for (int jj = 0; jj < C; ++jj) sp[jj] = lbase + jo[jj] * CF::GS;
 
   // split leaves run both halves; the loop stays rolled (half the code of
   // the unrolled form, which measured slower)
@@ -172,10 +185,12 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
     }
     fft_any<P, false>(w, t, spec, twr, tw);
     __syncwarp();
+    if constexpr (!(FF && C == 1)) {   // the other groups' operand (c = 1 fast-fold needs none)
 #pragma unroll
-    for (int m = 0; m < R1; ++m) {
-      if constexpr (PD == TT) *spec.cyc(t, m) = w[m];
-      else spec.st(t + TT * m, w[m]);
+      for (int m = 0; m < R1; ++m) {
+        if constexpr (PD == TT) *spec.cyc(t, m) = w[m];
+        else spec.st(t + TT * m, w[m]);
+      }
     }
     cp_async_wait_all();              // this branch's symbol row
     __syncthreads();
@@ -191,8 +206,8 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
         for (int j = 0; j < C; ++j) {
           const float2 sv = hi ? rowb[kr[j] + (N - b - t - TT * m)] : rowb[kr[j] + (t + TT * m)];
           const float sgn = hi ? sgf1[j] : sgf0[j];
-          const SmLine<PD, TT> sj{lbase + j * CF::GS};
-          const float2 xv = (PD == TT) ? *sj.cyc(t, m) : sj.ld(t + TT * m);
+          const SmLine<PD, TT> sj{sp[j]};
+          const float2 xv = (OWN && j == 0) ? w[m] : (PD == TT) ? *sj.cyc(t, m) : sj.ld(t + TT * m);
           // acc += sgn * (sv * xv): the parity sign rides on the accumulating FMA
           const float px = fmaf(sv.x, xv.x, -sv.y * xv.y);
           const float py = fmaf(sv.x, xv.y, sv.y * xv.x);
@@ -215,8 +230,8 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
         for (int j = 0; j < C; ++j) {
           float2 sv = __ldg(&Sd[off[pb][j] + fi]);
           if ((sg >> j) & 1) { sv.x = -sv.x; sv.y = -sv.y; }
-          const SmLine<PD, TT> sj{lbase + j * CF::GS};
-          acc = cadd(acc, cmul(sv, sj.ld(l)));
+          const SmLine<PD, TT> sj{sp[j]};
+          acc = cadd(acc, cmul(sv, (OWN && j == 0) ? w[m] : sj.ld(l)));
         }
         w[m] = acc;
       }
@@ -279,6 +294,7 @@ static cudaError_t leaf_reg_c(const LeafArgs& a, cudaStream_t st) {
     case 24: return leaf_reg_p<RP24, C>(a, st);
     case 48: return leaf_reg_p<RP48, C>(a, st);
     case 60: return leaf_reg_p<RP60, C>(a, st);
+    case 84: return leaf_reg_p<RP84, C>(a, st);
     case 96: return leaf_reg_p<RP96, C>(a, st);
     case 192: return leaf_reg_p<RP192, C>(a, st);
     case 160: return leaf_reg_p<RP160, C>(a, st);

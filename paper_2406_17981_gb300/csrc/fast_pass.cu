@@ -112,6 +112,7 @@ cudaError_t launch_pass_reg(int mode, const PassArgs& a, cudaStream_t st) {
     case 24: return pass_reg_p<RP24>(mode, a, st);
     case 48: return pass_reg_p<RP48>(mode, a, st);
     case 60: return pass_reg_p<RP60>(mode, a, st);
+    case 84: return pass_reg_p<RP84>(mode, a, st);
     case 96: return pass_reg_p<RP96>(mode, a, st);
     case 192: return pass_reg_p<RP192>(mode, a, st);
     case 160: return pass_reg_p<RP160>(mode, a, st);
