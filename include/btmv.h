@@ -176,22 +176,29 @@ BTMV_API btmv_status btmv_apply(btmv_plan p, const void* x, void* y, int nrhs, v
 
 /*
  * btmv_apply_batched -- y_k = T_k x_k for count independent plans, enqueued
- * as one persistent kernel launch on stream.
+ * on stream as one replay of a captured CUDA graph.
  *   plans, x, y, nrhs  host arrays of length count; entry k as in btmv_apply
  *                      (device pointers only).  Plans must be distinct.
- * SPLIT plans of one precision run together in one launch of a persistent
- * kernel: every plan's depth-first schedule (the launches btmv_apply would
- * make) becomes a chain of stages, stages of different plans run side by
- * side, and each wait for a previous stage is bounded (BTMV_WAIT_TIMEOUT_MS,
- * default 5000 ms).  The launch is captured once into a CUDA graph per
- * argument set (plans, x, y, nrhs) and replayed on later calls with the same
- * arguments; the first call for a new set of problem shapes also times a few
- * tile / radix choices on the caller's data and keeps the fastest (process
- * wide, and in the file named by BTMV_TUNE_CACHE if set).  Other mixes
- * (BTMV_ALGO_FULL plans, mixed precisions) run one apply after the other.
- * The first call for an argument set allocates its stage table; a wait that
- * expired in a launch is reported (BTMV_E_TIMEOUT) by the next call with the
- * same arguments.
+ * SPLIT plans of one precision run together.  The graph holds one of two
+ * execution modes:
+ *   0  one persistent kernel: every plan's depth-first schedule (the
+ *      launches btmv_apply would make) becomes a chain of stages, stages of
+ *      different plans run side by side, and each wait for a previous stage
+ *      is bounded (BTMV_WAIT_TIMEOUT_MS, default 5000 ms);
+ *   1  parallel branches (16, 4 or 1), each running its problems' own
+ *      btmv_apply launches; problems are placed largest first on the branch
+ *      with the least work.
+ * The graph is captured once per argument set (plans, x, y, nrhs) and
+ * replayed on later calls with the same arguments; the first call for a new
+ * set of problem shapes times the modes (and, for mode 0, a few tile / radix
+ * choices) on the caller's data and keeps the fastest (process wide, and in
+ * the file named by BTMV_TUNE_CACHE if set).  BTMV_NO_AUTOTUNE with
+ * BTMV_BATCH_MODE=0|1 fixes the mode instead; BTMV_BATCH_DIRECT runs the
+ * problems on forked streams without a graph (for mixes that change every
+ * call).  Other mixes (BTMV_ALGO_FULL plans, mixed precisions) run one
+ * apply after the other.  The first call for an argument set allocates its
+ * stage table; a wait that expired in a launch is reported (BTMV_E_TIMEOUT)
+ * by the next call with the same arguments.
  * Errors: as btmv_apply; on an argument error nothing is enqueued.
  */
 BTMV_API btmv_status btmv_apply_batched(int count, const btmv_plan* plans, const void* const* x,
@@ -234,9 +241,9 @@ BTMV_API btmv_status btmv_apply_host_noalloc(btmv_plan p, const void* x, void* y
  * cfg_out[0..7] = strided-pass tile lines, leaf lines per tile, leaf
  * right-hand sides per tile, radix order (0: 16 first, 1: 8 first), stages
  * of the persistent launch (mode 1: kernel launches per graph replay), work
- * items, blocks of the persistent launch, execution mode (0: one persistent
- * kernel, 1: one graph whose parallel branches run each problem's own
- * launches).  Arguments as for the
+ * items, blocks of the persistent launch (mode 1: parallel branches),
+ * execution mode (0: one persistent kernel, 1: one graph whose parallel
+ * branches run the problems' own launches, largest problems placed first).  Arguments as for the
  * btmv_apply_batched call.  Errors: BTMV_E_ARG, BTMV_E_STATE (no such batch).
  */
 BTMV_API btmv_status btmv_batch_tuning(int count, const btmv_plan* plans, const void* const* x,

@@ -35,20 +35,21 @@ using namespace btmv;
 
 namespace {
 
+constexpr int kBranchStreams = 16;
+
 struct TuneCfg {
   int mode = 0;    // 0: one persistent kernel; 1: graph with one branch per problem
   int TL = 0;      // strided-pass tile lines (0 = default)
   int Lt = 0;      // leaf lines per tile (0 = default)
   int rq = 0;      // leaf right-hand sides per tile (0 = default)
   int radix = 0;   // 0: radix-16 first, 1: radix-8 first
+  int nbr = 16;    // mode 1: parallel branches (problems placed largest first)
   std::string str() const {
-    char b[64];
-    snprintf(b, sizeof b, "%d %d %d %d %d", mode, TL, Lt, rq, radix);
+    char b[80];
+    snprintf(b, sizeof b, "%d %d %d %d %d %d", mode, TL, Lt, rq, radix, nbr);
     return b;
   }
 };
-
-constexpr int kBranchStreams = 16;
 
 struct Entry {
   std::vector<btmv_plan> plans;
@@ -73,6 +74,8 @@ struct Entry {
   bool launched = false;
   unsigned long long lru = 0;
   int cfg_mode = 0;                   // mode of the stage table / graph in place
+  int cfg_nbr = 1;                    // mode 1: branches in use
+  std::vector<int> branch;            // mode 1: branch of each problem
   int kernels = 0;                    // kernel nodes of the captured graph
   void* h_err_dev() const { return &((BatchCtl*)d_ctl)->error; }
 };
@@ -128,7 +131,9 @@ void load_tune_file() {
     if (!tab) continue;
     *tab = 0;
     TuneCfg c;
-    if (sscanf(tab + 1, "%d %d %d %d %d", &c.mode, &c.TL, &c.Lt, &c.rq, &c.radix) == 5) g_tuned[line] = c;
+    if (sscanf(tab + 1, "%d %d %d %d %d %d", &c.mode, &c.TL, &c.Lt, &c.rq, &c.radix, &c.nbr) == 6 && c.nbr >= 1 &&
+        c.nbr <= kBranchStreams)
+      g_tuned[line] = c;
   }
   fclose(f);
 }
@@ -193,8 +198,32 @@ btmv_status build_stages(const Entry& e, const TuneCfg& cfg, std::vector<BatchSt
   return BTMV_OK;
 }
 
+// Mode 1 placement: problems in decreasing order of vector bytes, each to
+// the branch with the least bytes so far (longest-processing-time first).
+void place_branches(Entry& e, int nbr) {
+  const int n = (int)e.plans.size();
+  nbr = std::max(1, std::min(nbr, std::min(kBranchStreams, std::max(1, n))));
+  e.cfg_nbr = nbr;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto bytes = [&](int i) {
+    double v = (double)e.nrhs[i] * e.plans[i]->c * (e.prec ? 16.0 : 8.0);
+    for (int m = 0; m < e.plans[i]->d; ++m) v *= e.plans[i]->n[m];
+    return v;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bytes(a) > bytes(b); });
+  std::vector<double> load(nbr, 0.0);
+  e.branch.assign(n, 0);
+  for (int i : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    e.branch[i] = k;
+    load[k] += bytes(i);
+  }
+}
+
 btmv_status upload(Entry& e, const TuneCfg& cfg) {
   e.cfg_mode = cfg.mode;
+  if (cfg.mode == 1) place_branches(e, cfg.nbr);
   std::vector<BatchStage> st;
   size_t smem = 0;
   if (cfg.mode == 0) build_stages(e, cfg, st, smem);
@@ -231,11 +260,11 @@ btmv_status enqueue_branches(Entry& e, cudaStream_t st) {
         return fail(BTMV_E_CUDA, "apply_batched: branch streams");
   }
   cudaEventRecord(e.fork, st);
-  const int nb = std::min<int>(kBranchStreams, (int)e.plans.size());
+  const int nb = e.cfg_nbr;
   for (int i = 0; i < nb; ++i) cudaStreamWaitEvent(e.bst[i], e.fork, 0);
   for (size_t i = 0; i < e.plans.size(); ++i) {
     if (!e.nrhs[i]) continue;
-    btmv_status s = btmv_apply_on_device(e.plans[i], e.x[i], e.y[i], e.nrhs[i], e.bst[i % nb]);
+    btmv_status s = btmv_apply_on_device(e.plans[i], e.x[i], e.y[i], e.nrhs[i], e.bst[e.branch[i]]);
     if (s != BTMV_OK) return s;
   }
   for (int i = 0; i < nb; ++i) {
@@ -298,9 +327,16 @@ float time_cfg(Entry& e, const TuneCfg& cfg, cudaStream_t st) {
 TuneCfg autotune(Entry& e, cudaStream_t st) {
   TuneCfg best;
   float bt = time_cfg(e, best, st);
+  // graph of branches: 16, 4 or 1 parallel branches
   TuneCfg br;
   br.mode = 1;
-  const float tb = time_cfg(e, br, st);
+  float tb = 1e30f;
+  for (int nb : {16, 4, 1}) {
+    TuneCfg c = br;
+    c.nbr = nb;
+    const float t = time_cfg(e, c, st);
+    if (t < tb) { tb = t; br = c; }
+  }
   if (tb < bt) return br;
   int maxr = 1;
   for (int r : e.nrhs) maxr = std::max(maxr, r);
@@ -497,7 +533,8 @@ extern "C" BTMV_API btmv_status btmv_batch_tuning(int count, const btmv_plan* pl
   if (!e) return fail(BTMV_E_STATE, "batch_tuning: no batch with these arguments has run");
   cfg_out[7] = e->cfg.mode;
   cfg_out[0] = e->cfg.TL; cfg_out[1] = e->cfg.Lt; cfg_out[2] = e->cfg.rq; cfg_out[3] = e->cfg.radix;
-  cfg_out[4] = e->cfg.mode == 1 ? e->kernels : e->nstages; cfg_out[5] = (int)std::min<long long>(e->nitems, 0x7fffffff); cfg_out[6] = e->grid;
+  cfg_out[4] = e->cfg.mode == 1 ? e->kernels : e->nstages; cfg_out[5] = (int)std::min<long long>(e->nitems, 0x7fffffff);
+  cfg_out[6] = e->cfg.mode == 1 ? e->cfg_nbr : e->grid;
   return BTMV_OK;
 }
 
