@@ -25,7 +25,11 @@ template <class P, int C> struct LeafCfg {
   // thread groups of a half-warp read together sit in opposite bank halves
   static constexpr int JP = ((P::N / 2 + 1 + 8) + 15) / 16 * 16;
   static __host__ __device__ constexpr int line_stride(int nsym) { return nsym * JP + 8; }
-  static constexpr int MINB = P::R3 == 1 ? (C == 1 ? 2 : (P::R1 <= 16 ? 5 : 2)) : 1; // blocks per SM to aim for
+  // blocks per SM to aim for; the c = 3 160- and 192-point plans run four with
+  // their stage twiddles read from the table (measured faster than two or
+  // three with register twiddles; the other composite plans spill at four)
+  static constexpr bool OCC4 = C == 3 && (P::N == 160 || P::N == 192);
+  static constexpr int MINB = OCC4 ? 4 : P::R3 == 1 ? (C == 1 ? 2 : (P::R1 <= 16 ? 5 : 2)) : 1;
   // dynamic smem: groups | phase table | staged symbol rows (nsym per line)
   static size_t smem(int nsym) {
     return ((size_t)LPC * C * GS + P::N + (size_t)LPC * line_stride(nsym)) * sizeof(float2);
@@ -127,8 +131,9 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
   for (int e = threadIdx.x; e < N; e += CF::THREADS) cp_async8(phs + e, ph + e);
   stage_row(0);
 
+  constexpr bool REGTW = P::R3 == 1 && !CF::OCC4;   // stage-2 twiddles held in registers
   TwReg<P> twr;
-  if constexpr (P::R3 == 1) twr.load(t, tw);
+  if constexpr (REGTW) twr.load(t, tw);
 
   // the input line is read once per half (the odd half's read hits in cache)
   // rather than held in registers across both halves
@@ -183,7 +188,8 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
       const float2 xv0 = ok ? xin[TT * m] : make_float2(0.f, 0.f);
       w[m] = b ? cmul(xv0, phs[t + TT * m]) : xv0;
     }
-    fft_any<P, false>(w, t, spec, twr, tw);
+    if constexpr (REGTW) fft_reg2<P, false>(w, t, spec, twr);
+    else fft_reg<P, false>(w, t, spec, tw);
     __syncwarp();
     if constexpr (!(FF && C == 1)) {   // the other groups' operand (c = 1 fast-fold needs none)
 #pragma unroll
@@ -238,7 +244,8 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
     }
     __syncthreads();
     if (b == 0 && a.split) stage_row(1);   // overlaps the inverse and the odd forward transform
-    fft_any<P, true>(w, t, spec, twr, tw);
+    if constexpr (REGTW) fft_reg2<P, true>(w, t, spec, twr);
+    else fft_reg<P, true>(w, t, spec, tw);
     if (a.split && b == 0) {
 #pragma unroll
       for (int m = 0; m < R1; ++m) stash[t + TT * m] = w[m];
