@@ -43,6 +43,8 @@ typedef RP<160, 20, 4, 2> RP160;
 typedef RP<320, 20, 4, 4> RP320;
 typedef RP<384, 24, 8, 2> RP384;
 typedef RP<768, 24, 4, 8> RP768;
+typedef RP<640, 40, 4, 4> RP640;
+typedef RP<1024, 16, 8, 8> RP1024;
 
 // shared-memory views of one line
 // Shared-memory views of one line.  ld/st take a point index p; cyc(t, m)
@@ -58,8 +60,8 @@ struct SmCol {            // [p][col] with W columns, col fastest
   __device__ __forceinline__ float2* ld2(int t, int q, int r) const { return base + (t * TT * W + (q * TT * TT + r) * W); }
   __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
-// One line owned by one warp-resident thread group, one pad slot every PD
-// points (PD = min(T, 16)).  With groups spaced by a stride that is T modulo
+// One line owned by one thread group (warp-resident for T <= 32), one pad
+// slot every PD points (PD = min(T, 16)).  With groups spaced by a stride that is T modulo
 // 16 (in 8-byte words), the stage-1 writes and stage-2 reads of all groups
 // sharing a half-warp fall into distinct banks.
 template <int PD, int TT>
@@ -72,7 +74,13 @@ struct SmLine {
   __device__ __forceinline__ float2* ld2(int t, int q, int r) const {
     return base + (t * (TT + 1) + q * TT * (TT + 1) + r);
   }
-  __device__ __forceinline__ void sync() const { __syncwarp(); }
+  // a group of up to 32 threads lies in one warp; longer lines (T = 64)
+  // span several warps and synchronise the whole block (every group of the
+  // block reaches the same barriers)
+  __device__ __forceinline__ void sync() const {
+    if constexpr (TT > 32) __syncthreads();
+    else __syncwarp();
+  }
 };
 
 template <class P> __host__ __device__ constexpr int pad_div() { return P::T < 16 ? P::T : 16; }
@@ -188,7 +196,7 @@ __device__ __forceinline__ void fft_any(float2 (&a)[P::R1], int t, const SM& sm,
 static inline bool reg_length(int N) {
   switch (N) {
     case 24: case 32: case 48: case 60: case 64: case 84: case 96: case 128: case 160: case 192: case 256: case 320:
-    case 384: case 512: case 768: return true;
+    case 384: case 512: case 640: case 768: case 1024: return true;
   }
   return false;
 }

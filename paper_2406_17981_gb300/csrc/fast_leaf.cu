@@ -13,8 +13,9 @@ namespace btmv {
 // the odd one is added with conj(P).  The plain embedding (a.split == 0)
 // runs a single 2n-point pass per line.
 template <class P, int C> struct LeafCfg {
-  // lines per block: 96 threads for c = 3, 128 for c = 1 (whole warps)
-  static constexpr int LPC = C == 1 ? 128 / P::T : 32 / P::T;
+  // lines per block: 96 threads for c = 3, 128 for c = 1 (whole warps);
+  // one line when its groups alone fill more (T = 64)
+  static constexpr int LPC = (C == 1 ? 128 / P::T : 32 / P::T) > 0 ? (C == 1 ? 128 / P::T : 32 / P::T) : 1;
   static constexpr int THREADS = LPC * C * P::T;
   static constexpr int SPN = padded_len<P>();
   static constexpr int BASE = SPN + P::N;                        // spectrum + stash
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
     }
     if constexpr (REGTW) fft_reg2<P, false>(w, t, spec, twr);
     else fft_reg<P, false>(w, t, spec, tw);
-    __syncwarp();
+    spec.sync();                      // the transform's last reads of the line buffer are done
     if constexpr (!(FF && C == 1)) {   // the other groups' operand (c = 1 fast-fold needs none)
 #pragma unroll
       for (int m = 0; m < R1; ++m) {
@@ -308,6 +309,8 @@ static cudaError_t leaf_reg_c(const LeafArgs& a, cudaStream_t st) {
     case 320: return leaf_reg_p<RP320, C>(a, st);
     case 384: return leaf_reg_p<RP384, C>(a, st);
     case 768: return leaf_reg_p<RP768, C>(a, st);
+    case 640: return leaf_reg_p<RP640, C>(a, st);
+    case 1024: return leaf_reg_p<RP1024, C>(a, st);
     case 32: return leaf_reg_p<RP32, C>(a, st);
     case 64: return leaf_reg_p<RP64, C>(a, st);
     case 128: return leaf_reg_p<RP128, C>(a, st);

@@ -5,8 +5,9 @@
 namespace btmv {
 
 // ------------------------------------------------------------- strided pass
-// columns per tile: 16 x 8 B = 128 B rows (8 for N = 512 to stay in 32 KB)
-template <class P> __host__ __device__ constexpr int pass_cols() { return P::N <= 256 ? 16 : 8; }
+// columns per tile: 16 x 8 B = 128 B rows; fewer for long lines so that the
+// tile stays within the 48 KB of static shared memory
+template <class P> __host__ __device__ constexpr int pass_cols() { return P::N <= 256 ? 16 : P::N <= 768 ? 8 : 4; }
 
 // minimum resident blocks per SM for the radix-16 plans of 128..512 points,
 // scaled to 128-thread blocks: 6 for the forward split (80 registers), 4 for
@@ -119,6 +120,8 @@ cudaError_t launch_pass_reg(int mode, const PassArgs& a, cudaStream_t st) {
     case 320: return pass_reg_p<RP320>(mode, a, st);
     case 384: return pass_reg_p<RP384>(mode, a, st);
     case 768: return pass_reg_p<RP768>(mode, a, st);
+    case 640: return pass_reg_p<RP640>(mode, a, st);
+    case 1024: return pass_reg_p<RP1024>(mode, a, st);
     case 32: return pass_reg_p<RP32>(mode, a, st);
     case 64: return pass_reg_p<RP64>(mode, a, st);
     case 128: return pass_reg_p<RP128>(mode, a, st);

@@ -266,6 +266,7 @@ template <int RAD, bool INV, class T> __device__ __forceinline__ void dft(T* a) 
   else if constexpr (RAD == 24) dft_pq<8, 3, INV>(a);
   else if constexpr (RAD == 30) dft_pq<6, 5, INV>(a);
   else if constexpr (RAD == 42) dft_pq<6, 7, INV>(a);
+  else if constexpr (RAD == 40) dft_pq<8, 5, INV>(a);
   else static_assert(RAD == 2, "radix not provided");
 }
 

@@ -174,7 +174,8 @@ REG_SIZES = [(32,), (64,), (128,), (256,), (512,), (32, 64), (8, 256), (512, 8),
              (16, 32, 64), (3, 128, 5), (128, 128, 16),
              (24,), (48,), (60,), (96,), (192,), (24, 48), (60, 12), (96, 24, 6), (12, 30, 48), (20, 192),
              (160,), (320,), (384,), (768,), (160, 12), (320, 20), (384, 6), (3, 768), (160, 8, 10),
-             (84,), (84, 24), (12, 10, 84), (84, 6, 14)]
+             (84,), (84, 24), (12, 10, 84), (84, 6, 14),
+             (640,), (1024,), (640, 6), (4, 1024), (3, 2, 640), (2, 3, 1024)]
 
 
 @pytest.mark.parametrize("n", REG_SIZES)
