@@ -83,7 +83,9 @@ enum {
 enum {
   BTMV_FLAG_NONE = 0,
   BTMV_FLAG_PROFILE = 1u << 0, /* record a CUDA event pair around every kernel
-                                  launch of btmv_apply (see btmv_profile_read) */
+                                  launch of btmv_apply (see btmv_profile_read);
+                                  with BTMV_PROFILE_EVERY=k in the environment
+                                  at plan creation, of one apply in every k */
   BTMV_FLAG_GENERIC = 1u << 1, /* use only the generic shared-memory line kernels
                                   (any 7-smooth size, both precisions) instead of
                                   the register-resident power-of-two kernels   */
@@ -314,7 +316,10 @@ enum {
 
 /*
  * btmv_profile_read -- with BTMV_FLAG_PROFILE, synchronise the events
- * recorded since the last read and return per-kernel-kind totals.
+ * recorded since the last read and return per-kernel-kind totals (over the
+ * sampled applies when BTMV_PROFILE_EVERY is set).  The events separate the
+ * launches they bracket, which then lose the programmatic-dependent-launch
+ * overlap of the register kernels.
  *   ms_total  host double[BTMV_K_NKINDS]: summed event-measured milliseconds.
  *   launches  host int64[BTMV_K_NKINDS]: launch counts.
  * Resets the accumulators.  Errors: BTMV_E_ARG, BTMV_E_STATE (flag not set),

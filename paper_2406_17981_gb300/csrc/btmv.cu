@@ -153,6 +153,11 @@ static btmv_status setup_two_streams(btmv_plan p, size_t V) {
   return BTMV_OK;
 }
 
+static void read_profile_every(btmv_plan p) {
+  const char* v = getenv("BTMV_PROFILE_EVERY");
+  p->prof_every = v && atoi(v) > 1 ? atoi(v) : 1;
+}
+
 extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n, int c, int precision,
                                         int algo, int max_rhs, uint32_t flags) {
   g_err.clear();
@@ -207,6 +212,7 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
   }
   st = setup_two_streams(p, V);
   if (st != BTMV_OK) { free_plan(p); return st; }
+  read_profile_every(p);
   *out = p;
   return BTMV_OK;
 }
@@ -238,6 +244,7 @@ extern "C" btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flag
     else
       p->W.push_back(p->ws);
   }
+  read_profile_every(p);
   *out = p;
   return BTMV_OK;
 }
@@ -431,7 +438,7 @@ struct ProfScope {
   cudaStream_t st;
   cudaEvent_t a = nullptr;
   ProfScope(btmv_plan p_, int k, cudaStream_t s) : p(p_), kind(k), st(s) {
-    if (p->flags & BTMV_FLAG_PROFILE) { a = get_event(p); cudaEventRecord(a, st); }
+    if (p->prof_on) { a = get_event(p); cudaEventRecord(a, st); }
     p->launches++;
   }
   ~ProfScope() {
@@ -750,6 +757,7 @@ static int is_device_ptr(const void* ptr) {
 }
 
 static btmv_status apply_device(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
+  p->prof_on = (p->flags & BTMV_FLAG_PROFILE) && (p->prof_count++ % p->prof_every) == 0;
   if (p->algo == BTMV_ALGO_SPLIT)
     return p->prec == BTMV_C64 ? split_apply<float2>(p, x, y, nrhs, st) : split_apply<double2>(p, x, y, nrhs, st);
   return p->prec == BTMV_C64 ? full_apply<float2>(p, x, y, nrhs, st) : full_apply<double2>(p, x, y, nrhs, st);

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "kernels.cuh"
 
 namespace btmv {
@@ -82,6 +84,35 @@ struct SmLine {
     else __syncwarp();
   }
 };
+
+// Programmatic dependent launch.  The register kernels are launched with
+// cudaLaunchAttributeProgrammaticStreamSerialization: the next kernel of the
+// stream is launched once every block of the running one has exited (the
+// implicit trigger), before that grid's completion and memory flush, so its
+// blocks are scheduled and run their prologue (index arithmetic, constant
+// tables, the symbol rows written at set-kernel time) while the previous
+// grid retires.  Data written by the previous kernel is read only after
+// grid_dep_wait(), which returns when that grid has completed and its
+// writes are visible.  (An explicit early trigger measured slower: waiting
+// blocks then shared the SMs with the previous kernel's last wave.)
+// Without the attribute the wait is a no-op.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 template <class P> __host__ __device__ constexpr int pad_div() { return P::T < 16 ? P::T : 16; }
 template <class P> __host__ __device__ constexpr int padded_len() { return P::N + P::N / pad_div<P>(); }

@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
 #pragma unroll
   for (int jj = 0; jj < C; ++jj) sp[jj] = lbase + jo[jj] * CF::GS;
 
+  grid_dep_wait();                    // the nodes written by the previous kernel
+
   // split leaves run both halves; the loop stays rolled (half the code of
   // the unrolled form, which measured slower)
   const int nbr = FF ? 2 : (a.split ? 2 : 1);
@@ -279,8 +281,12 @@ static cudaError_t leaf_reg_pf(const LeafArgs& a, cudaStream_t st) {
   }
   if (sm > 227 * 1024) return cudaErrorInvalidValue;
   dim3 grid((unsigned)nt, (unsigned)a.nnodes);
+#ifndef BTMV_NO_PDL
+  return launch_pdl(k_leaf_cg<P, C, FF>, grid, dim3(CF::THREADS), sm, st, a);
+#else
   k_leaf_cg<P, C, FF><<<grid, CF::THREADS, sm, st>>>(a);
   return cudaGetLastError();
+#endif
 }
 
 template <class P, int C>

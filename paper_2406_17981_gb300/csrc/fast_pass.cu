@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(pass_cols<P>() * P::T, pass_minb<P, MODE>()) k
   const float2* __restrict__ tw = (const float2*)a.fft.tw;
   const float2* __restrict__ ph = (const float2*)a.fft.ph;
   const SmCol<PW, TT> smc{sm + col};
+  grid_dep_wait();                                // the node written by the previous kernel
 
   if (MODE == 0) {
     const float2* __restrict__ in = (const float2*)a.in0;
@@ -90,9 +91,14 @@ static cudaError_t pass_reg_p(int mode, const PassArgs& a, cudaStream_t st) {
   constexpr int PW = pass_cols<P>();
   const long long nt = (a.g.lines + PW - 1) / PW;
   if (nt <= 0) return cudaSuccess;
+#ifndef BTMV_NO_PDL
+  if (mode == 0) return launch_pdl(k_pass_reg<P, 0>, dim3((unsigned)nt), dim3(PW * P::T), 0, st, a);
+  return launch_pdl(k_pass_reg<P, 1>, dim3((unsigned)nt), dim3(PW * P::T), 0, st, a);
+#else
   if (mode == 0) k_pass_reg<P, 0><<<(unsigned)nt, PW * P::T, 0, st>>>(a);
   else           k_pass_reg<P, 1><<<(unsigned)nt, PW * P::T, 0, st>>>(a);
   return cudaGetLastError();
+#endif
 }
 
 bool pass_reg_supported(const PassArgs& a, size_t esz) {

@@ -70,6 +70,11 @@ struct btmv_plan_s {
   double acc_ms[BTMV_K_NKINDS] = {0};
   int64_t acc_n[BTMV_K_NKINDS] = {0};
   int launches = 0;
+  // BTMV_FLAG_PROFILE: events around the launches of one apply in every
+  // prof_every (environment BTMV_PROFILE_EVERY, default 1)
+  int prof_every = 1;
+  long long prof_count = 0;
+  bool prof_on = false;
 };
 
 namespace btmv {
