@@ -145,8 +145,9 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
   // different components share a half-warp and the walk in the plain order
   // 0..C-1 keeps their shared-memory reads conflict-free (the same
   // spectrum, or buffers in opposite bank halves) and as few wavefronts, so
-  // OWN is used when a group fills its half-warps (T >= 16) or c = 1.
-  constexpr bool OWN = TT >= 16 || C == 1;
+  // OWN is used by the split leaf when a group fills its half-warps
+  // (T >= 16) or c = 1.
+  constexpr bool OWN = FF && (TT >= 16 || C == 1);   // (measured slower in the plain-embedding leaf)
   int jo[C];
 #pragma unroll
   for (int jj = 0; jj < C; ++jj) jo[jj] = !OWN ? jj : cc + jj < C ? cc + jj : cc + jj - C;

@@ -17,7 +17,7 @@ template <class P> __host__ __device__ constexpr int pass_cols() { return P::N <
 // and run unbounded.
 template <class P, int MODE> __host__ __device__ constexpr int pass_minb() {
   constexpr int b = (MODE == 0 ? 6 : 4) * 128 / (pass_cols<P>() * P::T);
-  return (P::R1 == 16 && P::N >= 128 && b > 0) ? b : 1;
+  return (P::R1 == 16 && P::N >= 128 && P::N <= 512 && b > 0) ? b : 1;
 }
 template <class P, int MODE>
 __global__ void __launch_bounds__(pass_cols<P>() * P::T, pass_minb<P, MODE>()) k_pass_reg(const PassArgs a) {
