@@ -74,9 +74,14 @@ enum {
 enum {
   BTMV_SYM_NONE = 0,
   BTMV_SYM_BLOCK = 1,      /* t_ab = t_ba: only blocks a <= b are read/stored   */
-  BTMV_SYM_PARITY = 2      /* per-(block, dim) parity t(-p_m) = +-t(p_m): the
+  BTMV_SYM_PARITY = 2,     /* per-(block, dim) parity t(-p_m) = +-t(p_m): the
                               generator is given on the non-negative orthant and
                               the symbol is stored mirror-compressed (Sec. II.C) */
+  BTMV_SYM_ADJOINT = 4     /* build the symbol of the conjugate transpose T^H
+                              (generator t^H_ab[p] = conj(t_ba[-p]); the other
+                              flags and parity describe the t passed in), for
+                              BiCG-type solvers.  The paper has no adjoint; the
+                              split algorithm is unchanged                     */
 };
 
 /* plan flags for btmv_plan_create (may be OR-ed) */

@@ -264,16 +264,69 @@ static int block_index(int c, bool bsym, int a, int b) {
   return -1;
 }
 
+// Generator of the conjugate transpose: T^H has blocks (T^H)_ab[i - j] =
+// conj(T_ba[j - i]), i.e. t^H_ab[p] = conj(t_ba[-p]).  Full layout: the
+// offset index p_m + n_m - 1 becomes (n_m - 1) - p_m (reversed along every
+// dim).  Orthant layout with parity: t_ba[-p] = (prod_m parity_ba[m]) t_ba[p]
+// for p >= 0, and t^H_ab has the parity of t_ba.  With block symmetry only
+// blocks a <= b of t are read, t_ba = t_ab.
+static void adjoint_generator(btmv_plan p, const double* t, const int8_t* parity, bool bsym,
+                              std::vector<double>& out, std::vector<int8_t>& par_out) {
+  const int d = p->d, c = p->c;
+  long long tb = 1;
+  int ext[MAX_D];
+  for (int m = 0; m < d; ++m) { ext[m] = parity ? p->n[m] : 2 * p->n[m] - 1; tb *= ext[m]; }
+  out.assign((size_t)c * c * tb * 2, 0.0);
+  if (parity) par_out.assign((size_t)c * c * d, 1);
+  for (int a = 0; a < c; ++a)
+    for (int b = 0; b < c; ++b) {
+      const int sa = bsym ? std::min(a, b) : b, sb = bsym ? std::max(a, b) : a;   // source block (b, a)
+      const double* src = t + ((size_t)sa * c + sb) * tb * 2;
+      double* dst = out.data() + ((size_t)a * c + b) * tb * 2;
+      double sign = 1.0;
+      if (parity)
+        for (int m = 0; m < d; ++m) {
+          const int8_t v = parity[((size_t)b * c + a) * d + m];
+          par_out[((size_t)a * c + b) * d + m] = v;
+          sign *= v;
+        }
+      for (long long i = 0; i < tb; ++i) {
+        long long j = i;
+        if (!parity) {           // reversed multi-index
+          long long r = i, acc = 0, stride = 1;
+          for (int m = d - 1; m >= 0; --m) {
+            const long long im = r % ext[m];
+            r /= ext[m];
+            acc += (ext[m] - 1 - im) * stride;
+            stride *= ext[m];
+          }
+          j = acc;
+        }
+        dst[2 * i] = sign * src[2 * j];
+        dst[2 * i + 1] = -sign * src[2 * j + 1];
+      }
+    }
+}
+
 extern "C" btmv_status btmv_set_kernel(btmv_plan p, const double* t, uint32_t sym_flags, const int8_t* parity,
                                        void* stream) {
   g_err.clear();
   if (!p) return fail(BTMV_E_ARG, "set_kernel: plan is NULL");
   if (!t) return fail(BTMV_E_ARG, "set_kernel: t is NULL");
-  if (sym_flags & ~(uint32_t)(BTMV_SYM_BLOCK | BTMV_SYM_PARITY)) return fail(BTMV_E_ARG, "set_kernel: unknown sym flags 0x%x", sym_flags);
+  if (sym_flags & ~(uint32_t)(BTMV_SYM_BLOCK | BTMV_SYM_PARITY | BTMV_SYM_ADJOINT))
+    return fail(BTMV_E_ARG, "set_kernel: unknown sym flags 0x%x", sym_flags);
   const bool bsym = (sym_flags & BTMV_SYM_BLOCK) != 0;
   const bool par = (sym_flags & BTMV_SYM_PARITY) != 0;
   const int d = p->d, c = p->c;
   if (par && !parity) return fail(BTMV_E_ARG, "set_kernel: BTMV_SYM_PARITY needs a parity array");
+  // BTMV_SYM_ADJOINT: replace (t, parity) by the generator of T^H on the host
+  std::vector<double> t_adj;
+  std::vector<int8_t> par_adj;
+  if (sym_flags & BTMV_SYM_ADJOINT) {
+    adjoint_generator(p, t, par ? parity : nullptr, bsym, t_adj, par_adj);
+    t = t_adj.data();
+    if (par) parity = par_adj.data();
+  }
   if (par) {
     for (int a = 0; a < c; ++a)
       for (int b = 0; b < c; ++b)

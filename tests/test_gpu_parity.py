@@ -277,3 +277,32 @@ def test_two_stream_schedule(n):
     y = yd.cpu().numpy().astype(np.complex128)
     assert rel(y, OE.embed_matvec(t, round_input(x, 0))) <= 1e-5
     assert rel(y, run_btmv(t, x, n, c, 0, 0)) <= 1e-6
+
+
+@pytest.mark.parametrize("n, c, form, algo", [((6, 5), 1, "full", 0), ((4, 3, 5), 3, "full", 0),
+                                              ((7, 6), 3, "block", 1), ((5, 4, 6), 3, "green", 0),
+                                              ((6, 8), 1, "skew1", 0), ((4, 6, 8), 3, "skew", 1)])
+def test_adjoint_symbol(n, c, form, algo):
+    """BTMV_SYM_ADJOINT: the apply equals conj(T)^T x, T the oracle's dense
+    matrix of the generator as given (every storage form)."""
+    par = None
+    if form == "full":
+        t = W.random_generator(n, c, seed=71)
+        tf, flags = t, 0
+    elif form == "block":
+        t = W.random_generator(n, c, seed=72)
+        t = 0.5 * (t + t.transpose(1, 0, *range(2, t.ndim)))          # t_ab = t_ba
+        tf, flags = t, bt.BTMV_SYM_BLOCK
+    elif form == "green":
+        t, par = W.green_dyadic_orthant(n, kh=0.45)
+        tf, flags = W.orthant_to_full(t, par), bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY
+    else:
+        t, par = W.skew_orthant(n, seed=73, c=c)
+        tf, flags = W.orthant_to_full(t, par), bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY
+    x = W.random_vector(n, c, seed=74, nrhs=2)
+    T = OT.dense_matrix(tf)
+    ref = (T.conj().T @ x.reshape(2, -1).T).T.reshape(x.shape)
+    y = run_btmv(t, x, n, c, 0, algo, flags | bt.BTMV_SYM_ADJOINT, par)
+    assert rel(y, ref) <= 1e-5
+    y2 = run_btmv(t, x, n, c, 1, algo, flags | bt.BTMV_SYM_ADJOINT, par)
+    assert rel(y2, ref) <= 1e-12
