@@ -68,3 +68,22 @@ def test_256_cubed_sampled_direct_sum(name):
     if cfg["kind"] == "skew":
         xr = x.astype(np.complex128)
         assert abs(np.sum(xr * y)) <= 1e-5 * np.linalg.norm(xr) * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("name", ["d3_128_c3_green_c64", "d3_256_c3_skew_c64"])
+def test_adjoint_identity_at_benchmark_size(name):
+    """<T x, z> = <x, T^H z> with T^H from BTMV_SYM_ADJOINT, at full size."""
+    cfg = W.WORKLOADS[name]
+    n = cfg["n"]
+    if cfg["kind"] == "green":
+        t, par = W.green_dyadic_orthant(n, kh=cfg["kh"])
+    else:
+        t, par = W.skew_orthant(n, seed=cfg["t_seed"])
+    x = W.random_vector(n, 3, seed=cfg["x_seed"]).astype(np.complex64)
+    z = W.random_vector(n, 3, seed=cfg["x_seed"] + 100).astype(np.complex64)
+    tx = _apply(n, t, par, 3, x)
+    thz = _apply(n, t, par, 3 | bt.BTMV_SYM_ADJOINT, z)
+    lhs = np.vdot(z.astype(np.complex128), tx)           # <T x, z> as z^H (T x)
+    rhs = np.vdot(thz, x.astype(np.complex128))          # (T^H z)^H x
+    scale = np.linalg.norm(tx) * np.linalg.norm(z)
+    assert abs(lhs - rhs) <= 1e-5 * scale
