@@ -113,7 +113,7 @@ enum {
 /*
  * btmv_plan_create -- allocate a plan for one problem geometry.
  *   out       [out] receives the plan handle (host pointer).
- *   d         number of Toeplitz levels, 1 <= d <= 4.
+ *   d         number of Toeplitz levels, 1 <= d <= 6 (BTMV_ALGO_FULL: d <= 4).
  *   n         host array of d level sizes, n[m] >= 1; every n[m] must factor
  *             into 2, 3, 5 and 7 and n[m] <= 1024 (BTMV_ALGO_FULL: 2 n[m] <= 2048).
  *   c         block size (components), 1 <= c <= 3.
@@ -280,7 +280,7 @@ BTMV_API const char* btmv_last_error(void);
  * ---------------------------------------------------------------------- */
 typedef struct {
   int d, c, precision, algo, max_rhs;
-  int n[4];
+  int n[6];
   int nsym;                 /* stored symbol blocks: c*c, or c(c+1)/2 with BTMV_SYM_BLOCK */
   int compressed;           /* 1 if the mirror-compressed parity store is in use */
   int has_symbol;

@@ -37,7 +37,7 @@ class BtmvError(RuntimeError):
 
 class btmv_plan_info_t(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("c", ctypes.c_int), ("precision", ctypes.c_int),
-                ("algo", ctypes.c_int), ("max_rhs", ctypes.c_int), ("n", ctypes.c_int * 4),
+                ("algo", ctypes.c_int), ("max_rhs", ctypes.c_int), ("n", ctypes.c_int * 6),
                 ("nsym", ctypes.c_int), ("compressed", ctypes.c_int), ("has_symbol", ctypes.c_int),
                 ("launches_per_apply", ctypes.c_int), ("symbol_bytes", ctypes.c_size_t),
                 ("workspace_bytes", ctypes.c_size_t), ("table_bytes", ctypes.c_size_t),

@@ -172,6 +172,8 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
   if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC | BTMV_FLAG_SHARED_RHS | BTMV_FLAG_TENSOR_CORE |
                           BTMV_FLAG_TWO_STREAMS))
     return fail(BTMV_E_ARG, "plan_create: unknown flags 0x%x", flags);
+  if (algo == BTMV_ALGO_FULL && d > 4)
+    return fail(BTMV_E_UNSUPPORTED, "plan_create: the plain embedding takes d <= 4 (d=%d)", d);
   for (int m = 0; m < d; ++m) {
     if (n[m] < 1) return fail(BTMV_E_ARG, "plan_create: n[%d]=%d < 1", m, n[m]);
     const int N = algo == BTMV_ALGO_FULL ? 2 * n[m] : n[m];

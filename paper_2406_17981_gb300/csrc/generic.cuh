@@ -18,8 +18,12 @@ static __host__ __device__ inline size_t pass_hdr_bytes(int TL) {
 }
 
 
+// per line of a leaf tile: the split-grid frequencies of its d-1 line dims
+// and a valid flag (last slot)
+constexpr int FPS = MAX_D;
+
 static __host__ __device__ inline size_t leaf_hdr_bytes(int Lt) {
-  return align_up((size_t)Lt * 4 * sizeof(int), 16);
+  return align_up((size_t)Lt * FPS * sizeof(int), 16);
 }
 
 
@@ -166,9 +170,9 @@ __device__ __forceinline__ void leaf_multiply(T* __restrict__ R, const LeafArgs&
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int li = dN.div(e);
     const int l = e - li * N;
-    if (fpre[li * 4 + 3] == 0) continue;   // line beyond the node
+    if (fpre[li * FPS + FPS - 1] == 0) continue;   // line beyond the node
     int f[MAX_D];
-    for (int m = 0; m < a.dl; ++m) f[m] = fpre[li * 4 + m];
+    for (int m = 0; m < a.dl; ++m) f[m] = fpre[li * FPS + m];
     f[a.dl] = a.split ? 2 * l + b : l;
     int fold, cls;
     const long long base = sym_index(a.sym, f, fold, cls);
@@ -241,12 +245,12 @@ __device__ __forceinline__ void leaf_multiply_tc(float2* __restrict__ R, const L
       fok[h] = e < nfreq;
       fl[h] = fok[h] ? e % N : 0;
       fli[h] = fok[h] ? e / N : 0;
-      if (fok[h] && fpre[fli[h] * 4 + 3] == 0) fok[h] = false;
+      if (fok[h] && fpre[fli[h] * FPS + FPS - 1] == 0) fok[h] = false;
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) sv[h][i][j] = make_float2(0.f, 0.f);
       if (!fok[h]) continue;
       int f[MAX_D];
-      for (int m = 0; m < a.dl; ++m) f[m] = fpre[fli[h] * 4 + m];
+      for (int m = 0; m < a.dl; ++m) f[m] = fpre[fli[h] * FPS + m];
       f[a.dl] = a.split ? 2 * fl[h] + b : fl[h];
       int fold, cls;
       const long long base = sym_index(a.sym, f, fold, cls);
@@ -322,7 +326,7 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, unsigned char* smem
   const int NV = rq * c * Lt;
   const int ls = N | 1;
   const int bufsz = NV * ls;
-  int* fpre = (int*)smem;                    // [Lt][4]: f of line dims, valid flag
+  int* fpre = (int*)smem;                    // [Lt][FPS]: f of line dims, valid flag
   T* X = (T*)(smem + leaf_hdr_bytes(Lt));
   T* B0 = X + bufsz;
   T* B1 = B0 + bufsz;
@@ -341,9 +345,9 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, unsigned char* smem
     for (int m = a.dl - 1; m >= 0; --m) {
       const int im = (int)(r % a.ext[m]);
       r /= a.ext[m];
-      fpre[li * 4 + m] = a.split ? 2 * im + ((nd.prefix >> m) & 1) : im;
+      fpre[li * FPS + m] = a.split ? 2 * im + ((nd.prefix >> m) & 1) : im;
     }
-    fpre[li * 4 + 3] = ok;
+    fpre[li * FPS + FPS - 1] = ok;
   }
   __syncthreads();
 
@@ -359,7 +363,7 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, unsigned char* smem
     const int ai = qa - qq * c;
     const int q = q0 + qq;
     T v = czero<T>();
-    if (fpre[li * 4 + 3] && q < a.nrhs)
+    if (fpre[li * FPS + FPS - 1] && q < a.nrhs)
       v = in[(long long)q * a.rhs_stride + (long long)ai * a.comp_stride + (l0 + li) * N + k];
     B0[vl * ls + k] = v;
     if (a.split) X[vl * ls + k] = cmul(v, __ldg(&ph[k]));
@@ -390,7 +394,7 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, unsigned char* smem
     const int qq = dc.div(qa);
     const int ai = qa - qq * c;
     const int q = q0 + qq;
-    if (!fpre[li * 4 + 3] || q >= a.nrhs) continue;
+    if (!fpre[li * FPS + FPS - 1] || q >= a.nrhs) continue;
     T v = A0[vl * ls + k];
     if (A1) v = cadd(v, cmulc(A1[vl * ls + k], __ldg(&ph[k])));
     out[(long long)q * a.rhs_stride + (long long)ai * a.comp_stride + (l0 + li) * N + k] = v;

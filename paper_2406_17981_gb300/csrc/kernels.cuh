@@ -42,7 +42,7 @@ struct PassArgs {
   FftDev fft;
 };
 
-constexpr int MAX_D = 4;
+constexpr int MAX_D = 6;               // split algorithm; the plain embedding takes d <= 4
 constexpr int MAX_CLS = 1 << MAX_D;
 
 struct SymDev {
@@ -75,7 +75,7 @@ struct LeafArgs {
   long long comp_stride;     // elements between components
   long long rhs_stride;      // elements between rhs
   int dl;                    // number of line dims (d - 1)
-  int ext[3];                // extents of the line dims
+  int ext[MAX_D - 1];        // extents of the line dims
   int split;                 // 1: split halves f = 2 l + b; 0: full grid f = l
   int tensor;                // 1: c x c x rq contraction on tensor cores (c = 3, complex64)
   long long tiles_per_node;

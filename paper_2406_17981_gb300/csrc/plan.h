@@ -34,7 +34,7 @@ struct TableSet {
 struct btmv_plan_s {
   int d = 0, c = 0, prec = 0, algo = 0, max_rhs = 0;
   uint32_t flags = 0;
-  int n[btmv::MAX_D] = {1, 1, 1, 1};
+  int n[btmv::MAX_D] = {1, 1, 1, 1, 1, 1};
   long long s = 1;          // prod n
   long long s2 = 1;         // prod 2n
   size_t esz = 8;           // bytes per complex

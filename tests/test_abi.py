@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol(L):
 
 @pytest.mark.parametrize("kw,status", [
     (dict(d=0, n=[4], c=1), bt.BTMV_E_ARG),
-    (dict(d=5, n=[4] * 5, c=1), bt.BTMV_E_ARG),
+    (dict(d=7, n=[4] * 7, c=1), bt.BTMV_E_ARG),
     (dict(d=1, n=[4], c=0), bt.BTMV_E_ARG),
     (dict(d=1, n=[4], c=4), bt.BTMV_E_ARG),
     (dict(d=1, n=[0], c=1), bt.BTMV_E_ARG),
@@ -40,6 +40,7 @@ def test_library_exports_every_declared_symbol(L):
     (dict(d=1, n=[4], c=1, flags=1 << 7), bt.BTMV_E_ARG),
     (dict(d=1, n=[11], c=1), bt.BTMV_E_UNSUPPORTED),
     (dict(d=2, n=[8, 2048], c=1), bt.BTMV_E_UNSUPPORTED),
+    (dict(d=5, n=[4] * 5, c=1, algo=1), bt.BTMV_E_UNSUPPORTED),
 ])
 def test_plan_create_rejects_bad_arguments(L, kw, status):
     args = dict(precision=bt.BTMV_C64, algo=bt.BTMV_ALGO_SPLIT, max_rhs=1, flags=0)

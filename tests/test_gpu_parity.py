@@ -306,3 +306,16 @@ def test_adjoint_symbol(n, c, form, algo):
     assert rel(y, ref) <= 1e-5
     y2 = run_btmv(t, x, n, c, 1, algo, flags | bt.BTMV_SYM_ADJOINT, par)
     assert rel(y2, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [(2, 3, 2, 3, 4), (3, 2, 4, 2, 2, 3), (2, 2, 2, 3, 32), (2, 3, 2, 2, 24, 2)])
+@pytest.mark.parametrize("c", [1, 3])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_five_and_six_levels(n, c, precision):
+    """d = 5 and 6 (Table 1's deeper levels), split algorithm, against the
+    oracle; the plain embedding stops at d = 4."""
+    t = W.random_generator(n, c, seed=90 + len(n))
+    x = W.random_vector(n, c, seed=91, nrhs=2)
+    y = run_btmv(t, x, n, c, precision, 0)
+    ref = OE.embed_matvec(t, round_input(x, precision))
+    assert rel(y, ref) <= TOL[precision]
