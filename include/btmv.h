@@ -322,7 +322,8 @@ enum {
 /*
  * btmv_profile_read -- with BTMV_FLAG_PROFILE, synchronise the events
  * recorded since the last read and return per-kernel-kind totals (over the
- * sampled applies when BTMV_PROFILE_EVERY is set).  The events separate the
+ * sampled applies when BTMV_PROFILE_EVERY is set; sampling restarts with the
+ * next apply, which is recorded).  The events separate the
  * launches they bracket, which then lose the programmatic-dependent-launch
  * overlap of the register kernels.
  *   ms_total  host double[BTMV_K_NKINDS]: summed event-measured milliseconds.

@@ -938,6 +938,7 @@ extern "C" btmv_status btmv_profile_read(btmv_plan p, double* ms_total, int64_t*
     p->acc_ms[k] = 0;
     p->acc_n[k] = 0;
   }
+  p->prof_count = 0;                  // the next apply is a sampled one
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(BTMV_E_CUDA, "profile_read: %s", cudaGetErrorString(e));
   return BTMV_OK;

@@ -210,6 +210,9 @@ WORKLOADS = {
     # d=3 256^3 dyadic Green, complex64
     "d3_256_c3_green_c64": dict(d=3, n=(256, 256, 256), c=3, kind="green", kh=KH_GREEN,
                                 x_seed=4, precision="c64"),
+    # d=3 192^3 dyadic Green, complex64 (the largest 3-d serving size; composite 192 = 24 x 8)
+    "d3_192_c3_green_c64": dict(d=3, n=(192, 192, 192), c=3, kind="green", kh=KH_GREEN,
+                                x_seed=8, precision="c64"),
     # d=3 256^3 skew (odd in every dim, t_ab = t_ba), complex64
     "d3_256_c3_skew_c64": dict(d=3, n=(256, 256, 256), c=3, kind="skew", t_seed=5,
                                x_seed=4, precision="c64"),
