@@ -212,6 +212,28 @@ BTMV_API btmv_status btmv_apply_batched(int count, const btmv_plan* plans, const
                                void* const* y, const int* nrhs, void* stream);
 
 /*
+ * btmv_apply_host_async -- y = T x with x and y in pinned HOST memory,
+ * pipelined across calls.  The call enqueues the copy of x into one of two
+ * plan-owned device staging slots (used in turn) on a plan copy stream, the
+ * apply on `stream`, and the copy of y back to the host on a second plan
+ * copy stream, and returns without waiting: consecutive calls on one plan
+ * overlap the copies of one call with the apply of the next.
+ *   p, nrhs   as btmv_apply.
+ *   x, y      host pointers (page-locked memory for the copies to overlap);
+ *             x must stay unchanged and y untouched until btmv_host_wait.
+ *   stream    the apply runs on it; a later btmv_apply on the same stream
+ *             follows the apply but not the copy of y.
+ * y is valid after btmv_host_wait(p).  The first call allocates the two
+ * slots (2 x 2 vectors of max_rhs right-hand sides) and the copy streams.
+ * Errors: as btmv_apply; BTMV_E_NOMEM on the first call.
+ */
+BTMV_API btmv_status btmv_apply_host_async(btmv_plan p, const void* x, void* y, int nrhs, void* stream);
+
+/* btmv_host_wait -- wait until every btmv_apply_host_async call made on p so
+ * far has its y on the host.  Errors: BTMV_E_ARG, BTMV_E_CUDA. */
+BTMV_API btmv_status btmv_host_wait(btmv_plan p);
+
+/*
  * btmv_apply_host_noalloc -- y = T x with x and y in HOST memory, like
  * btmv_apply with host pointers, but without allocating anything.
  *

@@ -59,6 +59,8 @@ def lib() -> ctypes.CDLL:
         L.btmv_set_kernel.argtypes = [vp, ctypes.POINTER(ctypes.c_double), u32, ctypes.POINTER(ctypes.c_int8), vp]
         L.btmv_apply.argtypes = [vp, vp, vp, i32, vp]
         L.btmv_apply_host_noalloc.argtypes = [vp, vp, vp, i32, vp]
+        L.btmv_apply_host_async.argtypes = [vp, vp, vp, i32, vp]
+        L.btmv_host_wait.argtypes = [vp]
         L.btmv_apply_batched.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                          ctypes.POINTER(ctypes.c_int), vp]
         L.btmv_destroy.argtypes = [vp]
@@ -142,6 +144,16 @@ def btmv_apply_host_noalloc(plan, x, y, nrhs, stream=None):
     """y = T x for host x, y staged through the library's fixed device array
     (no device allocation; see include/btmv.h for the size limit)."""
     _check(lib().btmv_apply_host_noalloc(plan, _ptr(x), _ptr(y), int(nrhs), _stream(stream)))
+
+
+def btmv_apply_host_async(plan, x, y, nrhs, stream=None):
+    """Pipelined y = T x for pinned host x, y; y is valid after
+    btmv_host_wait(plan)."""
+    _check(lib().btmv_apply_host_async(plan, _ptr(x), _ptr(y), int(nrhs), _stream(stream)))
+
+
+def btmv_host_wait(plan):
+    _check(lib().btmv_host_wait(plan))
 
 
 def btmv_apply_batched(plans, xs, ys, nrhs, stream=None):

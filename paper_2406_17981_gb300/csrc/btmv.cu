@@ -133,6 +133,15 @@ static void free_plan(btmv_plan p) {
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->stage_x) cudaFree(p->stage_x);
   if (p->stage_y) cudaFree(p->stage_y);
+  for (int s = 0; s < 2; ++s) {
+    if (p->ring_x[s]) cudaFree(p->ring_x[s]);
+    if (p->ring_y[s]) cudaFree(p->ring_y[s]);
+    if (p->ev_in[s]) cudaEventDestroy(p->ev_in[s]);
+    if (p->ev_comp[s]) cudaEventDestroy(p->ev_comp[s]);
+    if (p->ev_out[s]) cudaEventDestroy(p->ev_out[s]);
+  }
+  if (p->cp_in) cudaStreamDestroy(p->cp_in);
+  if (p->cp_out) cudaStreamDestroy(p->cp_out);
   delete p;
 }
 

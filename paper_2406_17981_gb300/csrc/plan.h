@@ -63,6 +63,13 @@ struct btmv_plan_s {
   // host staging
   void* stage_x = nullptr;
   void* stage_y = nullptr;
+  // btmv_apply_host_async: two staging slots used in turn, the copy streams
+  // and per-slot events (copy in done, apply done, copy out done)
+  void* ring_x[2] = {nullptr, nullptr};
+  void* ring_y[2] = {nullptr, nullptr};
+  cudaStream_t cp_in = nullptr, cp_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  long long pipe_k = 0;
   // profiling
   struct Rec { int kind; cudaEvent_t a, b; };
   std::vector<Rec> pending;

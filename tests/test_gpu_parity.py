@@ -319,3 +319,31 @@ def test_five_and_six_levels(n, c, precision):
     y = run_btmv(t, x, n, c, precision, 0)
     ref = OE.embed_matvec(t, round_input(x, precision))
     assert rel(y, ref) <= TOL[precision]
+
+
+def test_pipelined_host_applies():
+    """btmv_apply_host_async: a run of pipelined applies on pinned host
+    buffers gives each input's own result (bit for bit the synchronous
+    host-pointer apply), whatever the overlap of copies and applies."""
+    n, c = (24, 20, 32), 3
+    t, par = W.green_dyadic_orthant(n, kh=0.4)
+    plan = bt.Plan(n, c, 0, max_rhs=2)
+    plan.set_kernel(t, 3, par)
+    try:
+        xs = [torch.from_numpy(W.random_vector(n, c, seed=200 + k, nrhs=2).astype(np.complex64)).pin_memory()
+              for k in range(5)]
+        ys = [torch.zeros_like(x).pin_memory() for x in xs]
+        for k in range(12):                                  # slots reused several times
+            bt.btmv_apply_host_async(plan.handle, xs[k % 5], ys[k % 5], 2 if k % 3 else 1)
+        bt.btmv_host_wait(plan.handle)
+        for k in range(7, 12):                               # the last write of each y
+            r = 2 if k % 3 else 1
+            ya = np.zeros((r,) + xs[k % 5].shape[1:], dtype=np.complex64)
+            bt.btmv_apply(plan.handle, xs[k % 5].numpy()[:r].copy(), ya, r)
+            assert np.array_equal(ys[k % 5].numpy()[:r], ya), k
+        ref = OE.embed_matvec(W.orthant_to_full(t, par), xs[0].numpy().astype(np.complex128))
+        bt.btmv_apply_host_async(plan.handle, xs[0], ys[0], 2)
+        bt.btmv_host_wait(plan.handle)
+        assert rel(ys[0].numpy().astype(np.complex128), ref) <= 1e-5
+    finally:
+        plan.close()
