@@ -430,16 +430,25 @@ extern "C" BTMV_API btmv_status btmv_apply_batched(int count, const btmv_plan* p
   if (getenv("BTMV_BATCH_DIRECT")) {
     // argument sets that change every call (serving ticks): fork every
     // problem's schedule onto a pool of streams and join, without a graph
+    // (streams and events belong to a device: one pool per device)
+    constexpr int kMaxDev = 64;
     static std::mutex mu;
-    static cudaStream_t pool[kBranchStreams] = {};
-    static cudaEvent_t fork = nullptr, join[kBranchStreams] = {};
+    static cudaStream_t pools[kMaxDev][kBranchStreams] = {};
+    static cudaEvent_t forks[kMaxDev] = {}, joins[kMaxDev][kBranchStreams] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
+      return fail(BTMV_E_CUDA, "apply_batched: current device");
     std::lock_guard<std::mutex> lk(mu);
+    cudaStream_t* pool = pools[dev];
+    cudaEvent_t* join = joins[dev];
+    cudaEvent_t& fork = forks[dev];
     if (!fork) {
-      cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-      for (int i = 0; i < kBranchStreams; ++i) {
-        cudaStreamCreateWithFlags(&pool[i], cudaStreamNonBlocking);
-        cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
-      }
+      if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+        return fail(BTMV_E_CUDA, "apply_batched: fork event");
+      for (int i = 0; i < kBranchStreams; ++i)
+        if (cudaStreamCreateWithFlags(&pool[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) != cudaSuccess)
+          return fail(BTMV_E_CUDA, "apply_batched: branch streams");
     }
     const int nb = std::min(kBranchStreams, count);
     cudaEventRecord(fork, st);

@@ -275,12 +275,9 @@ static cudaError_t leaf_reg_pf(const LeafArgs& a, cudaStream_t st) {
   const long long nt = (total + CF::LPC - 1) / CF::LPC;
   if (nt <= 0 || a.nnodes <= 0) return cudaSuccess;
   const size_t sm = CF::smem(FF ? a.sym.nsym : 0);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_leaf_cg<P, C, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr = true;
-  }
   if (sm > 227 * 1024) return cudaErrorInvalidValue;
+  const cudaError_t ae = set_smem_attr<k_leaf_cg<P, C, FF>>(227 * 1024);
+  if (ae != cudaSuccess) return ae;
   dim3 grid((unsigned)nt, (unsigned)a.nnodes);
 #ifndef BTMV_NO_PDL
   return launch_pdl(k_leaf_cg<P, C, FF>, grid, dim3(CF::THREADS), sm, st, a);

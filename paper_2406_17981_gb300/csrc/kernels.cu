@@ -45,12 +45,13 @@ cudaError_t launch_pass(int mode, const PassArgs& a, cudaStream_t st) {
   const long long nt = (a.g.lines + a.g.TL - 1) / a.g.TL;
   if (nt <= 0) return cudaSuccess;
   if (nt > 0x7fffffffLL) return cudaErrorInvalidValue;
-  static bool attr0 = false, attr1 = false;
   if (mode == 0) {
-    if (!attr0) { cudaFuncSetAttribute(k_pass<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem); attr0 = true; }
+    const cudaError_t ae = set_smem_attr<k_pass<T, 0>>((int)kMaxSmem);
+    if (ae != cudaSuccess) return ae;
     k_pass<T, 0><<<(unsigned)nt, 256, sm, st>>>(a);
   } else {
-    if (!attr1) { cudaFuncSetAttribute(k_pass<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem); attr1 = true; }
+    const cudaError_t ae = set_smem_attr<k_pass<T, 1>>((int)kMaxSmem);
+    if (ae != cudaSuccess) return ae;
     k_pass<T, 1><<<(unsigned)nt, 256, sm, st>>>(a);
   }
   return cudaGetLastError();
@@ -68,8 +69,8 @@ cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t st) {
   if (sm > kMaxSmem) return cudaErrorInvalidValue;
   if (a.tiles_per_node <= 0 || a.nnodes <= 0) return cudaSuccess;
   if (a.tiles_per_node > 0x7fffffffLL || a.nnodes > MAX_LEAF_NODES) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(k_leaf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem); attr = true; }
+  const cudaError_t ae = set_smem_attr<k_leaf<T>>((int)kMaxSmem);
+  if (ae != cudaSuccess) return ae;
   dim3 grid((unsigned)a.tiles_per_node, (unsigned)a.nnodes);
   k_leaf<T><<<grid, 256, sm, st>>>(a);
   return cudaGetLastError();

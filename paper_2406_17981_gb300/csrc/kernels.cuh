@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/btmv.h"
 #include "fft.cuh"
 
@@ -126,6 +128,21 @@ struct BatchCtl {
   int withhold;              // self test: completion count a wait never reaches
   int pad;
 };
+
+// Opt a kernel in to more than 48 KB of dynamic shared memory on the
+// current device.  The attribute is per device, so the first launch on each
+// device sets it (devices 0..63).
+template <auto K>
+inline cudaError_t set_smem_attr(int bytes) {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
 
 // launchers (return cudaGetLastError())
 template <class T> cudaError_t launch_pass(int mode, const PassArgs& a, cudaStream_t st);

@@ -91,12 +91,8 @@ cudaError_t launch_persistent(const BatchStage* stages, int nstages, long long n
                               unsigned* done, long long timeout_ns, int grid, size_t smem, cudaStream_t st) {
   // the kernel also holds a few bytes of static shared memory
   const size_t dyn_max = kMaxSmem - 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  const cudaError_t e = set_smem_attr<k_persistent<T>>((int)dyn_max);
+  if (e != cudaSuccess) return e;
   if (smem + align_up(sizeof(BatchStage), 16) > dyn_max) return cudaErrorInvalidValue;
   k_persistent<T><<<grid, 256, smem + align_up(sizeof(BatchStage), 16), st>>>(stages, nstages, nitems, ctl, done,
                                                                             timeout_ns);
@@ -106,7 +102,7 @@ cudaError_t launch_persistent(const BatchStage* stages, int nstages, long long n
 template <class T>
 int persistent_blocks_per_sm(size_t smem) {
   int nb = 0;
-  cudaFuncSetAttribute(k_persistent<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSmem - 1024));
+  set_smem_attr<k_persistent<T>>((int)(kMaxSmem - 1024));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent<T>, 256, smem + align_up(sizeof(BatchStage), 16));
   return nb;
 }
