@@ -347,3 +347,32 @@ def test_pipelined_host_applies():
         assert rel(ys[0].numpy().astype(np.complex128), ref) <= 1e-5
     finally:
         plan.close()
+
+
+def test_stream_order_with_foreign_kernels():
+    """The register kernels start early (programmatic dependent launch) but
+    read their input only after the previous kernel of the stream: an input
+    written by a torch kernel right before each apply, and an output read
+    by one right after, match the oracle every time."""
+    n, c = (32, 24, 64), 3
+    t, par = W.green_dyadic_orthant(n, kh=0.3)
+    plan = bt.Plan(n, c, 0, max_rhs=1)
+    plan.set_kernel(t, 3, par)
+    try:
+        srcs = [W.random_vector(n, c, seed=300 + k).astype(np.complex64) for k in range(3)]
+        dsrc = [torch.from_numpy(v).cuda() for v in srcs]
+        x = torch.zeros_like(dsrc[0])
+        y = torch.zeros_like(x)
+        sums = []
+        for k in range(6):
+            x.copy_(dsrc[k % 3] * (k + 1))          # a torch kernel writes x just before the apply
+            plan.apply(x, y, 1)
+            sums.append((y * 2).sum())              # a torch kernel reads y just after
+        torch.cuda.synchronize()
+        tf = W.orthant_to_full(t, par)
+        for k in range(6):
+            ref = OE.embed_matvec(tf, srcs[k % 3].astype(np.complex128) * (k + 1))
+            got = complex(sums[k].item()) / 2
+            assert abs(got - ref.sum()) <= 1e-5 * np.abs(ref).sum(), k
+    finally:
+        plan.close()
