@@ -486,6 +486,24 @@ def run_batched(args):
     e1.record()
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1) / seq_steps
+    # the same batch forced into the one-persistent-kernel mode (a new argument
+    # set: fresh outputs), for comparison with the tuner's choice
+    os.environ["BTMV_NO_AUTOTUNE"] = "1"
+    os.environ["BTMV_BATCH_MODE"] = "0"
+    ys0 = [torch.empty_like(x) for x in xs]
+    try:
+        bt.btmv_apply_batched(handles, xs, ys0, nr)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(seq_steps):
+            bt.btmv_apply_batched(handles, xs, ys0, nr)
+        e1.record()
+        torch.cuda.synchronize()
+        pers_ms = e0.elapsed_time(e1) / seq_steps
+        pers_stages = bt.btmv_batch_tuning(handles, xs, ys0, nr)["stages"]
+    finally:
+        del os.environ["BTMV_NO_AUTOTUNE"]
+        del os.environ["BTMV_BATCH_MODE"]
     peaks, peak_src = measured_peaks()
     achieved = tot_bytes / (ms / args.steps / 1000.0) / 1e9
     for p in plans:
@@ -508,6 +526,8 @@ def run_batched(args):
                          "frac": achieved / float(peaks["hbm_gbs"]), "peak_source": f"{peak_src} hbm_gbs",
                          "traffic": None, "algorithmic_bytes_per_step": tot_bytes},
             "sequential_btmv_apply": {"ms_per_step": seq_ms, "matvecs_per_s": pairs / (seq_ms / 1000.0)},
+            "persistent_kernel_mode": {"ms_per_step": pers_ms, "matvecs_per_s": pairs / (pers_ms / 1000.0),
+                                       "stages": pers_stages},
             "gpu_launches": args.steps * (1 if tuning["mode"] == 0 else tuning["stages"]), "clocks": clocks}
     print(json.dumps(line))
 
