@@ -34,7 +34,7 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 WORKLOAD = "d3_128_c3_green_c64"
-PROFILE_EVERY = 10      # applies per event-profiled apply in the timed region
+PROFILE_EVERY = 50      # applies per event-profiled apply in the timed region
 L2_BYTES = 129 * 1024 * 1024
 METRIC = "block Toeplitz matvecs/s (split FFT, d=3 128^3 c=3 Green, complex64)"
 
