@@ -114,8 +114,14 @@ enum {
  * btmv_plan_create -- allocate a plan for one problem geometry.
  *   out       [out] receives the plan handle (host pointer).
  *   d         number of Toeplitz levels, 1 <= d <= 6 (BTMV_ALGO_FULL: d <= 4).
- *   n         host array of d level sizes, n[m] >= 1; every n[m] must factor
- *             into 2, 3, 5 and 7 and n[m] <= 1024 (BTMV_ALGO_FULL: 2 n[m] <= 2048).
+ *   n         host array of d level sizes, 1 <= n[m] <= 1024.  BTMV_ALGO_FULL
+ *             needs every n[m] to factor into 2, 3, 5 and 7.  A split plan
+ *             with other sizes (primes, ...; d <= 4) runs on the operator
+ *             zero-padded to the next 7-smooth size of each level -- exact,
+ *             since that operator restricted to the first n[m] points is T --
+ *             with x and y copied into and out of two padded device vectors
+ *             around each apply (btmv_get_symbol then returns the padded
+ *             operator's symbol).
  *   c         block size (components), 1 <= c <= 3.
  *   precision BTMV_C64 or BTMV_C128.
  *   algo      BTMV_ALGO_SPLIT or BTMV_ALGO_FULL.

@@ -424,7 +424,7 @@ extern "C" BTMV_API btmv_status btmv_apply_batched(int count, const btmv_plan* p
       if (plans[j] == plans[i]) return fail(BTMV_E_ARG, "apply_batched: plan %d repeated at %d", j, i);
     if (nrhs[i] && (!btmv_is_device_ptr(x[i]) || !btmv_is_device_ptr(y[i])))
       return fail(BTMV_E_ARG, "apply_batched: entry %d is not a device pointer", i);
-    if (plans[i]->algo != BTMV_ALGO_SPLIT || plans[i]->prec != plans[0]->prec) persistent = false;
+    if (plans[i]->algo != BTMV_ALGO_SPLIT || plans[i]->prec != plans[0]->prec || plans[i]->padded) persistent = false;
   }
   cudaStream_t st = (cudaStream_t)stream;
   if (getenv("BTMV_BATCH_DIRECT")) {

@@ -133,6 +133,8 @@ static void free_plan(btmv_plan p) {
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->stage_x) cudaFree(p->stage_x);
   if (p->stage_y) cudaFree(p->stage_y);
+  if (p->xpad) cudaFree(p->xpad);
+  if (p->ypad) cudaFree(p->ypad);
   for (int s = 0; s < 2; ++s) {
     if (p->ring_x[s]) cudaFree(p->ring_x[s]);
     if (p->ring_y[s]) cudaFree(p->ring_y[s]);
@@ -162,6 +164,24 @@ static btmv_status setup_two_streams(btmv_plan p, size_t V) {
   return BTMV_OK;
 }
 
+// Smallest 7-smooth size >= n that the FFT plans take (<= 1024), or -1.
+static int next_smooth(int n) {
+  for (int m = n; m <= 1024; ++m) {
+    FftDev f;
+    if (factor_radices(m, f)) return m;
+  }
+  return -1;
+}
+
+// Padded plans: device copies of x and y at the padded sizes (V bytes each).
+static btmv_status setup_padding(btmv_plan p, size_t V) {
+  if (!p->padded) return BTMV_OK;
+  if (cudaMalloc(&p->xpad, V) != cudaSuccess || cudaMalloc(&p->ypad, V) != cudaSuccess)
+    return fail(BTMV_E_NOMEM, "plan: padded x and y of %zu bytes", V);
+  p->ws_bytes += 2 * V;
+  return BTMV_OK;
+}
+
 static void read_profile_every(btmv_plan p) {
   const char* v = getenv("BTMV_PROFILE_EVERY");
   p->prof_every = v && atoi(v) > 1 ? atoi(v) : 1;
@@ -183,17 +203,33 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
     return fail(BTMV_E_ARG, "plan_create: unknown flags 0x%x", flags);
   if (algo == BTMV_ALGO_FULL && d > 4)
     return fail(BTMV_E_UNSUPPORTED, "plan_create: the plain embedding takes d <= 4 (d=%d)", d);
+  int np[MAX_D];
   for (int m = 0; m < d; ++m) {
     if (n[m] < 1) return fail(BTMV_E_ARG, "plan_create: n[%d]=%d < 1", m, n[m]);
-    const int N = algo == BTMV_ALGO_FULL ? 2 * n[m] : n[m];
+    if (n[m] > 1024) return fail(BTMV_E_UNSUPPORTED, "plan_create: n[%d]=%d > 1024", m, n[m]);
     FftDev f;
-    if (n[m] > 1024 || !factor_radices(N, f))
-      return fail(BTMV_E_UNSUPPORTED, "plan_create: n[%d]=%d must be <= 1024 and 7-smooth", m, n[m]);
+    if (algo == BTMV_ALGO_FULL) {
+      if (!factor_radices(2 * n[m], f))
+        return fail(BTMV_E_UNSUPPORTED, "plan_create: the plain embedding needs 7-smooth sizes (n[%d]=%d)", m, n[m]);
+      np[m] = n[m];
+    } else {
+      np[m] = next_smooth(n[m]);
+      if (np[m] < 0)
+        return fail(BTMV_E_UNSUPPORTED, "plan_create: no 7-smooth size <= 1024 at or above n[%d]=%d", m, n[m]);
+    }
   }
+  bool padded = false;
+  for (int m = 0; m < d; ++m) padded = padded || np[m] != n[m];
+  if (padded && d > 4) return fail(BTMV_E_UNSUPPORTED, "plan_create: sizes that are not 7-smooth need d <= 4");
   btmv_plan p = new btmv_plan_s();
   p->d = d; p->c = c; p->prec = precision; p->algo = algo; p->max_rhs = max_rhs; p->flags = flags;
   p->esz = precision == BTMV_C64 ? sizeof(float2) : sizeof(double2);
-  for (int m = 0; m < d; ++m) { p->n[m] = n[m]; p->s *= n[m]; p->s2 *= 2 * n[m]; }
+  p->padded = padded;
+  for (int m = 0; m < d; ++m) {
+    p->nu[m] = n[m]; p->su *= n[m];
+    p->n[m] = np[m]; p->s *= np[m]; p->s2 *= 2 * np[m];
+  }
+  n = p->n;                        // the padded sizes from here on
   if (cudaGetDevice(&p->dev) != cudaSuccess) { free_plan(p); return fail(BTMV_E_CUDA, "plan_create: no CUDA device"); }
 
   std::vector<int> Nf, Nd;
@@ -223,6 +259,8 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
   }
   st = setup_two_streams(p, V);
   if (st != BTMV_OK) { free_plan(p); return st; }
+  st = setup_padding(p, V);
+  if (st != BTMV_OK) { free_plan(p); return st; }
   read_profile_every(p);
   *out = p;
   return BTMV_OK;
@@ -240,6 +278,8 @@ extern "C" btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flag
   p->d = src->d; p->c = src->c; p->prec = src->prec; p->algo = src->algo; p->max_rhs = max_rhs; p->flags = flags;
   for (int m = 0; m < MAX_D; ++m) { p->n[m] = src->n[m]; p->fft_apply[m] = src->fft_apply[m]; p->fft_sym[m] = src->fft_sym[m]; }
   p->s = src->s; p->s2 = src->s2; p->esz = src->esz; p->dev = src->dev;
+  for (int m = 0; m < MAX_D; ++m) p->nu[m] = src->nu[m];
+  p->su = src->su; p->padded = src->padded;
   p->tab = src->tab;                                  // shared twiddle tables
   p->sym = src->sym; p->sym_owner = src->sym_owner;   // shared symbol store
   p->sym_bytes = src->sym_bytes; p->symdev = src->symdev; p->has_sym = src->has_sym;
@@ -254,6 +294,10 @@ extern "C" btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flag
       for (size_t i = 0; i < nvec; ++i) p->W.push_back((unsigned char*)p->ws + i * V);
     else
       p->W.push_back(p->ws);
+  }
+  {
+    const btmv_status st = setup_padding(p, V);
+    if (st != BTMV_OK) { free_plan(p); return st; }
   }
   read_profile_every(p);
   *out = p;
@@ -286,7 +330,7 @@ static void adjoint_generator(btmv_plan p, const double* t, const int8_t* parity
   const int d = p->d, c = p->c;
   long long tb = 1;
   int ext[MAX_D];
-  for (int m = 0; m < d; ++m) { ext[m] = parity ? p->n[m] : 2 * p->n[m] - 1; tb *= ext[m]; }
+  for (int m = 0; m < d; ++m) { ext[m] = parity ? p->nu[m] : 2 * p->nu[m] - 1; tb *= ext[m]; }
   out.assign((size_t)c * c * tb * 2, 0.0);
   if (parity) par_out.assign((size_t)c * c * d, 1);
   for (int a = 0; a < c; ++a)
@@ -319,6 +363,36 @@ static void adjoint_generator(btmv_plan p, const double* t, const int8_t* parity
     }
 }
 
+// Padded plans: the generator given at the caller's sizes nu, zero outside
+// them, laid out at the padded sizes n (full layout: offset p_m at
+// p_m + n_m - 1; orthant layout: p_m >= 0).  The padded operator restricted
+// to the first nu_m points of every level is the caller's operator.
+static void pad_generator(btmv_plan p, const double* t, bool orthant, std::vector<double>& out) {
+  const int d = p->d, c = p->c;
+  int eu[MAX_D], ep[MAX_D], sh[MAX_D];
+  long long tu = 1, tp = 1;
+  for (int m = 0; m < d; ++m) {
+    eu[m] = orthant ? p->nu[m] : 2 * p->nu[m] - 1;
+    ep[m] = orthant ? p->n[m] : 2 * p->n[m] - 1;
+    sh[m] = orthant ? 0 : p->n[m] - p->nu[m];      // offset index shift
+    tu *= eu[m];
+    tp *= ep[m];
+  }
+  out.assign((size_t)c * c * tp * 2, 0.0);
+  for (int blk = 0; blk < c * c; ++blk)
+    for (long long i = 0; i < tu; ++i) {
+      long long r = i, j = 0, stride = 1;
+      for (int m = d - 1; m >= 0; --m) {
+        const long long im = r % eu[m];
+        r /= eu[m];
+        j += (im + sh[m]) * stride;
+        stride *= ep[m];
+      }
+      out[((size_t)blk * tp + j) * 2] = t[((size_t)blk * tu + i) * 2];
+      out[((size_t)blk * tp + j) * 2 + 1] = t[((size_t)blk * tu + i) * 2 + 1];
+    }
+}
+
 extern "C" btmv_status btmv_set_kernel(btmv_plan p, const double* t, uint32_t sym_flags, const int8_t* parity,
                                        void* stream) {
   g_err.clear();
@@ -337,6 +411,11 @@ extern "C" btmv_status btmv_set_kernel(btmv_plan p, const double* t, uint32_t sy
     adjoint_generator(p, t, par ? parity : nullptr, bsym, t_adj, par_adj);
     t = t_adj.data();
     if (par) parity = par_adj.data();
+  }
+  std::vector<double> t_pad;
+  if (p->padded) {
+    pad_generator(p, t, par, t_pad);
+    t = t_pad.data();
   }
   if (par) {
     for (int a = 0; a < c; ++a)
@@ -820,11 +899,33 @@ static int is_device_ptr(const void* ptr) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Padded plans: x is copied into the padded buffer (zeros outside the
+// caller's sizes), the apply runs at the padded sizes, and the caller's part
+// of the padded result is copied to y.
+template <class T>
+static btmv_status pad_copy(btmv_plan p, const void* src, void* dst, int nrhs, bool to_pad, cudaStream_t st) {
+  PadArgs a;
+  memset(&a, 0, sizeof a);
+  a.src = src; a.dst = dst; a.d = p->d; a.to_pad = to_pad ? 1 : 0;
+  for (int m = 0; m < p->d; ++m) { a.nu[m] = p->nu[m]; a.np[m] = p->n[m]; }
+  a.total = (long long)nrhs * p->c * (to_pad ? p->s : p->su);
+  ProfScope ps(p, BTMV_K_COPY, st);
+  const cudaError_t e = launch_pad<T>(a, st);
+  if (e != cudaSuccess) return fail(BTMV_E_CUDA, "padding copy: %s", cudaGetErrorString(e));
+  return BTMV_OK;
+}
+
 static btmv_status apply_device(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
   p->prof_on = (p->flags & BTMV_FLAG_PROFILE) && (p->prof_count++ % p->prof_every) == 0;
+  const bool c64 = p->prec == BTMV_C64;
+  if (p->padded) {
+    TRY(c64 ? pad_copy<float2>(p, x, p->xpad, nrhs, true, st) : pad_copy<double2>(p, x, p->xpad, nrhs, true, st));
+    TRY(c64 ? split_apply<float2>(p, p->xpad, p->ypad, nrhs, st) : split_apply<double2>(p, p->xpad, p->ypad, nrhs, st));
+    return c64 ? pad_copy<float2>(p, p->ypad, y, nrhs, false, st) : pad_copy<double2>(p, p->ypad, y, nrhs, false, st);
+  }
   if (p->algo == BTMV_ALGO_SPLIT)
-    return p->prec == BTMV_C64 ? split_apply<float2>(p, x, y, nrhs, st) : split_apply<double2>(p, x, y, nrhs, st);
-  return p->prec == BTMV_C64 ? full_apply<float2>(p, x, y, nrhs, st) : full_apply<double2>(p, x, y, nrhs, st);
+    return c64 ? split_apply<float2>(p, x, y, nrhs, st) : split_apply<double2>(p, x, y, nrhs, st);
+  return c64 ? full_apply<float2>(p, x, y, nrhs, st) : full_apply<double2>(p, x, y, nrhs, st);
 }
 
 static btmv_status check_apply(btmv_plan p, const void* x, void* y, int nrhs) {
@@ -834,7 +935,7 @@ static btmv_status check_apply(btmv_plan p, const void* x, void* y, int nrhs) {
   if (nrhs == 0) return BTMV_OK;
   if (!x || !y) return fail(BTMV_E_ARG, "apply: x or y is NULL");
   if (((uintptr_t)x | (uintptr_t)y) & 15) return fail(BTMV_E_ARG, "apply: x and y must be 16-byte aligned");
-  const size_t V = (size_t)nrhs * p->c * p->s * p->esz;
+  const size_t V = (size_t)nrhs * p->c * p->su * p->esz;
   const char* xa = (const char*)x;
   const char* ya = (const char*)y;
   if (xa < ya + V && ya < xa + V) return fail(BTMV_E_ARG, "apply: x and y overlap");
@@ -846,7 +947,7 @@ static btmv_status check_apply(btmv_plan p, const void* x, void* y, int nrhs) {
 btmv_status btmv_check_apply_args(btmv_plan p, const void* x, void* y, int nrhs) {
   return check_apply(p, x, y, nrhs);
 }
-size_t btmv_apply_vector_bytes(btmv_plan p, int nrhs) { return (size_t)nrhs * p->c * p->s * p->esz; }
+size_t btmv_apply_vector_bytes(btmv_plan p, int nrhs) { return (size_t)nrhs * p->c * p->su * p->esz; }
 btmv_status btmv_apply_on_device(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
   p->launches = 0;
   return apply_device(p, x, y, nrhs, st);
@@ -863,8 +964,8 @@ extern "C" btmv_status btmv_apply(btmv_plan p, const void* x, void* y, int nrhs,
   p->launches = 0;
   if (dx && dy) return apply_device(p, x, y, nrhs, st);
   // host staging
-  const size_t V = (size_t)nrhs * p->c * p->s * p->esz;
-  const size_t Vmax = (size_t)p->max_rhs * p->c * p->s * p->esz;
+  const size_t V = (size_t)nrhs * p->c * p->su * p->esz;
+  const size_t Vmax = (size_t)p->max_rhs * p->c * p->su * p->esz;
   if (!dx && !p->stage_x) CUDA_TRY(cudaMalloc(&p->stage_x, Vmax));
   if (!dy && !p->stage_y) CUDA_TRY(cudaMalloc(&p->stage_y, Vmax));
   const void* xd = x;
@@ -914,7 +1015,7 @@ extern "C" btmv_status btmv_plan_get_info(btmv_plan p, btmv_plan_info_t* info) {
   if (!p || !info) return fail(BTMV_E_ARG, "plan_get_info: NULL argument");
   memset(info, 0, sizeof *info);
   info->d = p->d; info->c = p->c; info->precision = p->prec; info->algo = p->algo; info->max_rhs = p->max_rhs;
-  for (int m = 0; m < MAX_D; ++m) info->n[m] = m < p->d ? p->n[m] : 0;
+  for (int m = 0; m < MAX_D; ++m) info->n[m] = m < p->d ? p->nu[m] : 0;
   info->nsym = p->nsym;
   info->compressed = p->compressed;
   info->has_symbol = p->has_sym ? 1 : 0;
@@ -922,7 +1023,7 @@ extern "C" btmv_status btmv_plan_get_info(btmv_plan p, btmv_plan_info_t* info) {
   info->symbol_bytes = p->sym_bytes;
   info->workspace_bytes = p->ws_bytes;
   info->table_bytes = p->tab.bytes;
-  info->vector_bytes = (size_t)p->c * p->s * p->esz;
+  info->vector_bytes = (size_t)p->c * p->su * p->esz;
   return BTMV_OK;
 }
 

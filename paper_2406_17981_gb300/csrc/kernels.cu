@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "generic.cuh"
 
 namespace btmv {
@@ -75,6 +77,40 @@ cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t st) {
   k_leaf<T><<<grid, 256, sm, st>>>(a);
   return cudaGetLastError();
 }
+
+// ------------------------------------------------------------------- pad
+template <class T>
+__global__ void __launch_bounds__(256) k_pad(const PadArgs a) {
+  const int* wn = a.to_pad ? a.np : a.nu;     // shape of the written vector
+  const int* on = a.to_pad ? a.nu : a.np;     // shape of the other one
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < a.total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e, src = 0, stride = 1;
+    bool inside = true;
+    for (int m = a.d - 1; m >= 0; --m) {
+      const int im = (int)(r % wn[m]);
+      r /= wn[m];
+      inside = inside && im < on[m] && im < wn[m];
+      src += (long long)im * stride;
+      stride *= on[m];
+    }
+    src += r * stride;                        // (rhs, component) index
+    T v;
+    v.x = 0; v.y = 0;
+    if (inside) v = ((const T*)a.src)[src];
+    ((T*)a.dst)[e] = v;
+  }
+}
+
+template <class T>
+cudaError_t launch_pad(const PadArgs& a, cudaStream_t st) {
+  if (a.total <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((a.total + 255) / 256, 152LL * 16);
+  k_pad<T><<<(unsigned)blocks, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_pad<float2>(const PadArgs&, cudaStream_t);
+template cudaError_t launch_pad<double2>(const PadArgs&, cudaStream_t);
 
 // ----------------------------------------------------------------- symbol
 // F[kk][k] = scale * sum_{h in {0,1}^d} (-1)^{<h, b>} c~_kk[k + h n]  with

@@ -144,6 +144,18 @@ inline cudaError_t set_smem_attr(int bytes) {
   return e;
 }
 
+// Copy between a vector of the caller's sizes nu and one of the padded sizes
+// np (same [r][c][..] layout): to_pad = 1 writes every padded element (zero
+// outside nu), 0 writes the nu-part back.
+struct PadArgs {
+  const void* src;
+  void* dst;
+  int d, to_pad;
+  int nu[MAX_D], np[MAX_D];
+  long long total;           // elements of the written vector
+};
+template <class T> cudaError_t launch_pad(const PadArgs& a, cudaStream_t st);
+
 // launchers (return cudaGetLastError())
 template <class T> cudaError_t launch_pass(int mode, const PassArgs& a, cudaStream_t st);
 template <class T> cudaError_t launch_leaf(const LeafArgs& a, cudaStream_t st);

@@ -36,6 +36,14 @@ struct btmv_plan_s {
   uint32_t flags = 0;
   int n[btmv::MAX_D] = {1, 1, 1, 1, 1, 1};
   long long s = 1;          // prod n
+  // sizes the caller uses.  A split plan whose sizes are not all 7-smooth
+  // runs on the operator zero-padded to the next 7-smooth sizes (n above);
+  // x and y are copied into and out of the padded buffers around the apply
+  int nu[btmv::MAX_D] = {1, 1, 1, 1, 1, 1};
+  long long su = 1;         // prod nu
+  bool padded = false;
+  void* xpad = nullptr;
+  void* ypad = nullptr;
   long long s2 = 1;         // prod 2n
   size_t esz = 8;           // bytes per complex
   int dev = 0;

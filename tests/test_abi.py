@@ -38,7 +38,8 @@ def test_library_exports_every_declared_symbol(L):
     (dict(d=1, n=[4], c=1, algo=9), bt.BTMV_E_ARG),
     (dict(d=1, n=[4], c=1, max_rhs=0), bt.BTMV_E_ARG),
     (dict(d=1, n=[4], c=1, flags=1 << 7), bt.BTMV_E_ARG),
-    (dict(d=1, n=[11], c=1), bt.BTMV_E_UNSUPPORTED),
+    (dict(d=1, n=[11], c=1, algo=1), bt.BTMV_E_UNSUPPORTED),
+    (dict(d=5, n=[4, 4, 4, 4, 11], c=1), bt.BTMV_E_UNSUPPORTED),
     (dict(d=2, n=[8, 2048], c=1), bt.BTMV_E_UNSUPPORTED),
     (dict(d=5, n=[4] * 5, c=1, algo=1), bt.BTMV_E_UNSUPPORTED),
 ])

@@ -376,3 +376,39 @@ def test_stream_order_with_foreign_kernels():
             assert abs(got - ref.sum()) <= 1e-5 * np.abs(ref).sum(), k
     finally:
         plan.close()
+
+
+@pytest.mark.parametrize("n", [(11,), (13, 7), (17, 5, 4), (127, 3), (3, 2, 101), (61, 9), (2, 3, 4, 13)])
+@pytest.mark.parametrize("c", [1, 3])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sizes_that_are_not_seven_smooth(n, c, precision):
+    """Prime and other non-7-smooth sizes: the split plan runs the operator
+    zero-padded to the next 7-smooth sizes and returns the caller's part."""
+    t = W.random_generator(n, c, seed=400 + sum(n))
+    x = W.random_vector(n, c, seed=401, nrhs=2)
+    y = run_btmv(t, x, n, c, precision, 0)
+    ref = OE.embed_matvec(t, round_input(x, precision))
+    assert rel(y, ref) <= TOL[precision]
+    yh = run_btmv(t, x, n, c, precision, 0, host=True)             # host pointers (staging)
+    assert rel(yh, ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("n", [(13, 11, 7), (31, 17, 29)])
+def test_padded_green_parity_and_adjoint(n):
+    """Compressed parity store and the adjoint on a padded (prime-size) plan."""
+    t, par = W.green_dyadic_orthant(n, kh=0.3)
+    tf = W.orthant_to_full(t, par)
+    x = W.random_vector(n, 3, seed=402, nrhs=1)
+    y = run_btmv(t, x, n, 3, 0, 0, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+    assert rel(y, OE.embed_matvec(tf, round_input(x, 0))) <= 1e-5
+    plan = bt.Plan(n, 3, 0)
+    assert tuple(plan.info["n"]) == n
+    plan.close()
+    tz, parz = W.skew_orthant(n, seed=403)
+    yf = run_btmv(tz, x, n, 3, 1, 0, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, parz)
+    assert rel(yf, OE.embed_matvec(W.orthant_to_full(tz, parz), x)) <= 1e-12
+    z = W.random_vector(n, 3, seed=404, nrhs=1)
+    yz = run_btmv(tz, z, n, 3, 1, 0, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY | bt.BTMV_SYM_ADJOINT, parz)
+    lhs = np.vdot(z, yf)
+    rhs = np.vdot(yz, x)
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(yf) * np.linalg.norm(z)
