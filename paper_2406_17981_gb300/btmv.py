@@ -239,6 +239,16 @@ class Plan:
         btmv_apply(self.handle, x, y, nrhs, stream)
         return y
 
+    def apply_host_async(self, x, y, nrhs=None, stream=None):
+        """Pipelined apply on pinned host buffers; y is valid after host_wait()."""
+        if nrhs is None:
+            nrhs = x.shape[0] if len(x.shape) == self.d + 2 else 1
+        btmv_apply_host_async(self.handle, x, y, nrhs, stream)
+        return y
+
+    def host_wait(self):
+        btmv_host_wait(self.handle)
+
     def close(self):
         if self.handle:
             btmv_destroy(self.handle)
