@@ -33,7 +33,7 @@ class SolveSpec:
     matvec budget."""
 
     def __init__(self, n, c, t, parity, sym_flags, alpha, b_seed, max_matvecs=60, tol=1e-6, arrival=0.0,
-                 name=""):
+                 name="", abort_after=None):
         self.n = tuple(int(v) for v in n)
         self.c = int(c)
         self.t, self.parity, self.sym_flags = t, parity, sym_flags
@@ -43,6 +43,9 @@ class SolveSpec:
         self.tol = float(tol)
         self.arrival = float(arrival)
         self.name = name
+        # the client gives up after this many matvecs (its solve leaves the
+        # server unfinished); None: runs to convergence or max_matvecs
+        self.abort_after = abort_after
 
     @property
     def op_key(self):
@@ -95,6 +98,7 @@ class Solve:
         self.phase = "start"
         self.matvecs = 0
         self.done = False
+        self.aborted = False
         self.resid = 1.0
         self.algo = algo
 
@@ -104,6 +108,10 @@ class Solve:
 
     def step(self) -> bool:
         th = self.torch
+        if self.spec.abort_after is not None and self.matvecs >= self.spec.abort_after:
+            self.aborted = True                    # the client went away mid-solve
+            self.done = True
+            return False
         vd = lambda a, b: th.vdot(a.flatten(), b.flatten())  # noqa: E731
         al = self.spec.alpha
         if self.phase == "start":
@@ -191,7 +199,7 @@ class Server:
         batch_sizes = []
         matvecs = 0
         t0 = time.perf_counter()
-        finished = []
+        finished, aborted = [], []
         while pending or active or inflight:
             now = time.perf_counter() - t0
             # admission by arrival time and HBM budget
@@ -226,7 +234,11 @@ class Server:
                     elif s.done:
                         active.remove(s)
                         used -= s.spec.footprint()
-                        finished.append(s)
+                        if s.aborted:
+                            aborted.append(s)
+                            s.plan.close()                   # its workspace goes back at once
+                        else:
+                            finished.append(s)
             # launch the ready requests as one batch
             if ready and len(inflight) < self.max_inflight:
                 batch, ready = ready, []
@@ -259,7 +271,8 @@ class Server:
             "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
             "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
             "batches": nbatches, "mean_batch": float(np.mean(batch_sizes)) if batch_sizes else 0.0,
-            "peak_active_solves": peak_active, "solves": len(finished),
+            "peak_active_solves": peak_active, "solves": len(finished), "aborted": len(aborted),
+            "budget_in_use_at_end": used,
             "max_residual": max((s.resid for s in finished), default=0.0),
             "solutions": {s.spec.name: s.x for s in finished},
             "rhs": {s.spec.name: s.b for s in finished},

@@ -86,3 +86,40 @@ def test_admission_respects_the_hbm_budget():
     out = serve.Server(budget_bytes=budget).run(specs)
     assert out["solves"] == 4
     assert out["peak_active_solves"] <= 2
+
+
+def _alone(spec):
+    return serve.Server(budget_bytes=8 * 10 ** 9).run([serve.SolveSpec(
+        spec.n, spec.c, spec.t, spec.parity, spec.sym_flags, spec.alpha, spec.b_seed,
+        spec.max_matvecs, spec.tol, 0.0, spec.name)])
+
+
+def test_client_that_aborts_mid_solve():
+    """A client that goes away after a few matvecs leaves the server: its
+    workspace is released, and every other solve still equals its result
+    alone."""
+    specs = make_specs(SHAPES[:4])
+    specs[1].abort_after = 3
+    out = serve.Server(budget_bytes=8 * 10 ** 9).run(specs)
+    assert out["aborted"] == 1 and out["solves"] == 3
+    assert specs[1].name not in out["solutions"]
+    for spec in (specs[0], specs[2], specs[3]):
+        a = _alone(spec)["solutions"][spec.name].cpu().numpy().astype(np.complex128)
+        m = out["solutions"][spec.name].cpu().numpy().astype(np.complex128)
+        assert rel(m, a) <= 1e-4, spec.name
+    # only the resident operators' symbols are still counted against the budget
+    assert out["budget_in_use_at_end"] == sum(s.symbol_footprint() for s in specs)
+
+
+def test_aborted_solve_frees_room_for_a_waiting_one():
+    n = (16, 16, 16)
+    t, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)              # one operator, shared symbol
+    flags = bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY
+    alpha = serve.scaled_alpha(t, par, flags, n, 3)
+    specs = [serve.SolveSpec(n, 3, t, par, flags, alpha, b_seed=500 + k, max_matvecs=40, tol=1e-5,
+                             arrival=0.0, name=f"w{k}", abort_after=2 if k == 0 else None) for k in range(2)]
+    budget = specs[0].symbol_footprint() + specs[0].footprint() + 1     # one solve at a time
+    out = serve.Server(budget_bytes=budget).run(specs)
+    assert out["aborted"] == 1 and out["solves"] == 1
+    assert out["peak_active_solves"] == 1
+    assert out["max_residual"] <= 1e-4
