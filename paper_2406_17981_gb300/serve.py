@@ -4,11 +4,14 @@ Many solves (BiCGSTAB on A = I - alpha T, T a block Toeplitz operator) run at
 once.  Each admitted solve keeps its plan (symbol, twiddles, workspace) and
 its Krylov vectors resident on the GPU; solves are admitted in arrival order
 while their device footprint fits an HBM budget, and leave (freeing their
-memory) when they finish.  Every scheduler tick gathers the matvec requests
-of all solves that are ready and runs them as ONE btmv_apply_batched launch
-(one persistent kernel across all of them); while a batch is on the GPU the
+memory) when they finish or their client goes away.  Every scheduler tick
+gathers the matvec requests of all solves that are ready and enqueues them as
+ONE btmv_apply_batched call (each problem's launches forked onto a pool of
+streams, since the mix changes every tick); while a batch is on the GPU the
 host admits newcomers, runs the Krylov updates of finished requests and forms
-the next batch, with up to ``max_inflight`` batches queued on the device.
+the next batch, with up to ``max_inflight`` batches queued on the device.  A
+batch whose launch fails is retried one solve at a time; a solve whose own
+apply fails as well leaves the server and is reported.
 
 The matvec is the library's (C ABI); the Krylov updates are plain torch
 vector operations on the device.  Latency of a request = time from the moment
@@ -185,6 +188,26 @@ class Server:
             self.ops[spec.op_key] = master
         return Solve(spec, self.ops[spec.op_key].clone(1), self.torch, self.algo)
 
+    def _launch(self, batch, st):
+        """Enqueue the batch's matvecs on st; returns (solves launched, solves
+        lost).  A batch whose launch fails is retried one solve at a time;
+        a solve whose own apply fails too is lost (reported by run)."""
+        if self.batched:
+            try:
+                bt.btmv_apply_batched([s.plan.handle for s in batch], [s.xin for s in batch],
+                                      [s.yout for s in batch], [1] * len(batch), stream=st)
+                return batch, []
+            except bt.BtmvError:
+                pass                                           # retried one at a time below
+        ok, lost = [], []
+        for s in batch:
+            try:
+                bt.btmv_apply(s.plan.handle, s.xin, s.yout, 1, stream=st)
+                ok.append(s)
+            except bt.BtmvError:
+                lost.append(s)
+        return ok, lost
+
     def run(self, specs):
         th = self.torch
         if self.batched:
@@ -199,7 +222,7 @@ class Server:
         batch_sizes = []
         matvecs = 0
         t0 = time.perf_counter()
-        finished, aborted = [], []
+        finished, aborted, failed = [], [], []
         while pending or active or inflight:
             now = time.perf_counter() - t0
             # admission by arrival time and HBM budget
@@ -244,12 +267,15 @@ class Server:
                 batch, ready = ready, []
                 st = self.streams[nbatches % self.max_inflight]
                 st.wait_stream(self.upd)                     # the batch reads the updated inputs
-                if self.batched:
-                    bt.btmv_apply_batched([s.plan.handle for s in batch], [s.xin for s in batch],
-                                          [s.yout for s in batch], [1] * len(batch), stream=st)
-                else:
-                    for s in batch:
-                        bt.btmv_apply(s.plan.handle, s.xin, s.yout, 1, stream=st)
+                batch, lost = self._launch(batch, st)
+                for s in lost:                               # reported, removed, budget share returned
+                    active.remove(s)
+                    used -= s.spec.footprint()
+                    t_ready.pop(id(s), None)
+                    s.plan.close()
+                    failed.append(s)
+                if not batch:
+                    continue
                 ev = th.cuda.Event()
                 ev.record(st)
                 inflight.append((ev, batch, time.perf_counter()))
@@ -272,6 +298,7 @@ class Server:
             "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
             "batches": nbatches, "mean_batch": float(np.mean(batch_sizes)) if batch_sizes else 0.0,
             "peak_active_solves": peak_active, "solves": len(finished), "aborted": len(aborted),
+            "failed": len(failed), "failed_names": [s.spec.name for s in failed],
             "budget_in_use_at_end": used,
             "max_residual": max((s.resid for s in finished), default=0.0),
             "solutions": {s.spec.name: s.x for s in finished},

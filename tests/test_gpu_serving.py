@@ -123,3 +123,62 @@ def test_aborted_solve_frees_room_for_a_waiting_one():
     assert out["aborted"] == 1 and out["solves"] == 1
     assert out["peak_active_solves"] == 1
     assert out["max_residual"] <= 1e-4
+
+
+def test_failed_batch_is_retried_one_solve_at_a_time(monkeypatch):
+    """Host-side fault: the batched call fails once; the server retries the
+    batch's solves one at a time and every result equals its alone result."""
+    specs = make_specs(SHAPES[:4])
+    real = serve.bt.btmv_apply_batched
+    calls = {"n": 0}
+
+    def flaky(*args, **kw):
+        calls["n"] += 1
+        if calls["n"] == 2:
+            raise bt.BtmvError(bt.BTMV_E_CUDA, "injected failure")
+        return real(*args, **kw)
+
+    monkeypatch.setattr(serve.bt, "btmv_apply_batched", flaky)
+    out = serve.Server(budget_bytes=8 * 10 ** 9).run(specs)
+    assert calls["n"] >= 2 and out["failed"] == 0 and out["solves"] == len(specs)
+    for spec in specs:
+        a = _alone(spec)["solutions"][spec.name].cpu().numpy().astype(np.complex128)
+        m = out["solutions"][spec.name].cpu().numpy().astype(np.complex128)
+        assert rel(m, a) <= 1e-4, spec.name
+
+
+def test_solve_whose_apply_fails_is_reported(monkeypatch):
+    """Host-side fault: batches always fail and one solve's own apply fails
+    too; that solve is reported and removed, the others finish as alone."""
+    specs = make_specs(SHAPES[:4])
+    server = serve.Server(budget_bytes=8 * 10 ** 9)
+
+    def fail_batch(*args, **kw):
+        raise bt.BtmvError(bt.BTMV_E_CUDA, "injected batch failure")
+
+    real_apply = serve.bt.btmv_apply
+    bad = {}
+
+    def apply(handle, x, y, nrhs, stream=None):
+        if bad and handle == bad.get("h"):
+            raise bt.BtmvError(bt.BTMV_E_CUDA, "injected apply failure")
+        return real_apply(handle, x, y, nrhs, stream=stream)
+
+    real_admit = server._admit
+
+    def admit(spec):
+        s = real_admit(spec)
+        if spec.name == "s2":
+            bad["h"] = s.plan.handle
+        return s
+
+    monkeypatch.setattr(serve.bt, "btmv_apply_batched", fail_batch)
+    monkeypatch.setattr(serve.bt, "btmv_apply", apply)
+    monkeypatch.setattr(server, "_admit", admit)
+    out = server.run(specs)
+    assert out["failed"] == 1 and out["failed_names"] == ["s2"] and out["solves"] == 3
+    monkeypatch.undo()                                  # the alone runs use the real calls
+    for spec in (specs[0], specs[1], specs[3]):
+        a = _alone(spec)["solutions"][spec.name].cpu().numpy().astype(np.complex128)
+        m = out["solutions"][spec.name].cpu().numpy().astype(np.complex128)
+        assert rel(m, a) <= 1e-4, spec.name
