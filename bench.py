@@ -35,6 +35,7 @@ import workloads as W  # noqa: E402
 
 WORKLOAD = "d3_128_c3_green_c64"
 PROFILE_EVERY = 50      # applies per event-profiled apply in the timed region
+CHUNK = 50              # timed-region steps per chunk for the per-step percentiles
 L2_BYTES = 129 * 1024 * 1024
 METRIC = "block Toeplitz matvecs/s (split FFT, d=3 128^3 c=3 Green, complex64)"
 
@@ -298,14 +299,22 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    marks = [(0, e0)]                        # an event every CHUNK steps: per-step time spread
     e0.record()
     for i in range(args.steps):
+        if i and i % CHUNK == 0:
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record()
+            marks.append((i, ev))
         plan.apply(xs[i % npool], ys[i % npool], 1)
     e1.record()
+    marks.append((args.steps, e1))
     torch.cuda.synchronize()
     barrier(ws)
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
+    chunk_ms = [a[1].elapsed_time(b[1]) / (b[0] - a[0]) for a, b in zip(marks, marks[1:]) if b[0] > a[0]]
+    spread = [float(v) for v in np.percentile(chunk_ms, [10, 50, 90])] if len(chunk_ms) >= 3 else None
     ms_max = max_over_ranks(ms, ws)
     prof = bt.btmv_profile_read(plan.handle)
     sampled = (args.steps + PROFILE_EVERY - 1) // PROFILE_EVERY   # applies 0, k, 2k, .. after the read
@@ -403,7 +412,8 @@ def main():
         return
     line = {
         "metric": metric_name(cfg), "value": value, "unit": "matvecs/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "ms_per_step_p10_p50_p90": spread, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == bt.BTMV_C64 else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "d": len(n), "n": list(n), "c": c, "nrhs": 1,
