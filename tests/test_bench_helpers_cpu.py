@@ -1,0 +1,24 @@
+"""bench.py helpers that run without a GPU: metric names per workload, and
+the rule that a recorded ncu DRAM figure is used only while the kernel's
+sources are unchanged."""
+import bench
+import workloads as W
+
+
+def test_metric_names():
+    assert bench.metric_name(W.WORKLOADS["d3_128_c3_green_c64"]) == bench.METRIC
+    assert "256^3" in bench.metric_name(W.WORKLOADS["d3_256_c3_skew_c64"])
+    assert "complex128" in bench.metric_name(W.WORKLOADS["d2_64_c1_random_c128"])
+
+
+def test_ncu_traffic_follows_the_kernel_sources(monkeypatch):
+    v = bench.ncu_traffic("leaf", "d3_128_c3_green_c64")
+    assert v is not None and v > 1e8                    # the committed summary matches the sources
+    assert bench.ncu_traffic("leaf", "no_such_workload") is None
+    monkeypatch.setattr(bench, "source_sha", lambda kind=None: "0" * 16)
+    assert bench.ncu_traffic("leaf", "d3_128_c3_green_c64") is None   # stale once the kernel changes
+
+
+def test_source_sha_depends_on_the_kind():
+    assert bench.source_sha("leaf") != bench.source_sha("fwd_split")
+    assert len(bench.source_sha()) == 16
