@@ -20,6 +20,8 @@ btmv_status btmv_check_apply_args(btmv_plan p, const void* x, void* y, int nrhs)
 size_t btmv_apply_vector_bytes(btmv_plan p, int nrhs);
 btmv_status btmv_apply_on_device(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st);
 btmv_status btmv_set_error(btmv_status st, const char* msg);
+void btmv_clear_error();
+int btmv_plan_device(btmv_plan p);
 
 namespace {
 
@@ -30,13 +32,18 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_stage_ptr[kMaxDevices] = {nullptr};
 
-// Device address of g_stage on the current device (looked up once per device,
-// with that device current).  In host code the name g_stage is only a host
-// stand-in, so the address must come from cudaGetSymbolAddress.
-btmv_status stage_address(void** out) {
+// Device address of g_stage on the plan's device, which must be the current
+// one (looked up once per device, with that device current).  In host code
+// the name g_stage is only a host stand-in, so the address must come from
+// cudaGetSymbolAddress.
+btmv_status stage_address(int plan_dev, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return btmv_set_error(BTMV_E_CUDA, "apply_host_noalloc: cudaGetDevice failed");
+  // the staging array of another device would be read by kernels that run on
+  // the plan's device, next to the plan's symbol, tables and workspace
+  if (dev != plan_dev)
+    return btmv_set_error(BTMV_E_ARG, "apply_host_noalloc: the current device is not the plan's device");
   if (dev < 0 || dev >= kMaxDevices) return btmv_set_error(BTMV_E_UNSUPPORTED, "apply_host_noalloc: device index too large");
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_stage_ptr[dev]) {
@@ -54,6 +61,7 @@ btmv_status stage_address(void** out) {
 
 extern "C" BTMV_API btmv_status btmv_apply_host_noalloc(btmv_plan p, const void* x, void* y, int nrhs,
                                                         void* stream) {
+  btmv_clear_error();
   btmv_status st = btmv_check_apply_args(p, x, y, nrhs);
   if (st != BTMV_OK) return st;
   if (nrhs == 0) return BTMV_OK;
@@ -63,7 +71,7 @@ extern "C" BTMV_API btmv_status btmv_apply_host_noalloc(btmv_plan p, const void*
                           "apply_host_noalloc: nrhs * c * prod(n) * element size exceeds "
                           "BTMV_NOALLOC_MAX_BYTES (16 MiB); use btmv_apply");
   void* base = nullptr;
-  st = stage_address(&base);
+  st = stage_address(btmv_plan_device(p), &base);
   if (st != BTMV_OK) return st;
   unsigned char* xs = (unsigned char*)base;
   unsigned char* ys = xs + BTMV_NOALLOC_MAX_BYTES;

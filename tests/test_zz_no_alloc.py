@@ -76,3 +76,65 @@ def test_noalloc_rejects_vectors_beyond_the_limit():
         assert rel(y2.astype(np.complex128), _device_apply(plan, x2).astype(np.complex128)) <= 1e-5
     finally:
         plan.close()
+
+
+def test_noalloc_allocates_no_device_memory():
+    """The property the entry point exists for: once the library's staging
+    array is resident (the first call on the device), calls on a freshly
+    created plan leave the device's free memory unchanged."""
+    n, c, r = (24, 20, 16), 3, 2
+    t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    x = W.random_vector(n, c, seed=44, nrhs=r).astype(np.complex64)
+    y = np.zeros_like(x)
+    warm = bt.Plan(n, c, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=r)
+    warm.set_kernel(t_orth, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+    plan = bt.Plan(n, c, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=r)
+    plan.set_kernel(t_orth, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+    try:
+        bt.btmv_apply_host_noalloc(warm.handle, x, y, r)   # loads the array and the kernels
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(4):
+            bt.btmv_apply_host_noalloc(plan.handle, x, y, r)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert rel(y.astype(np.complex128), _device_apply(plan, x).astype(np.complex128)) <= 1e-5
+    finally:
+        warm.close()
+        plan.close()
+
+
+def test_noalloc_padded_size_on_a_torch_stream():
+    """Sizes that are not 7-smooth (23 is prime) run zero-padded inside the
+    plan; the call is issued on a non-default torch stream."""
+    n, c, r = (23, 20, 16), 3, 1
+    t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    plan = bt.Plan(n, c, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=r)
+    plan.set_kernel(t_orth, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+    stream = torch.cuda.Stream()
+    try:
+        for seed in (45, 46):
+            x = W.random_vector(n, c, seed=seed, nrhs=r).astype(np.complex64)
+            y = np.full_like(x, np.nan)
+            bt.btmv_apply_host_noalloc(plan.handle, x, y, r, stream=stream)
+            assert np.all(np.isfinite(y))
+            assert rel(y.astype(np.complex128), _device_apply(plan, x).astype(np.complex128)) <= 1e-5
+    finally:
+        plan.close()
+
+
+def test_noalloc_success_clears_an_earlier_error():
+    n, c = (8, 8, 8), 3
+    t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    plan = bt.Plan(n, c, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=1)
+    plan.set_kernel(t_orth, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+    try:
+        x = W.random_vector(n, c, seed=47).astype(np.complex64)
+        y = np.zeros_like(x)
+        with pytest.raises(bt.BtmvError):
+            bt.btmv_apply_host_noalloc(plan.handle, x, y, 2)     # nrhs beyond the plan's max_rhs
+        assert bt.btmv_last_error() != ""
+        bt.btmv_apply_host_noalloc(plan.handle, x, y, 1)
+        assert bt.btmv_last_error() == ""
+    finally:
+        plan.close()
