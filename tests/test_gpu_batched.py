@@ -11,7 +11,7 @@ import pytest
 
 import workloads as W
 from oracle import embed as OE
-from tests.gpu_util import rel, round_input
+from tests.gpu_util import batched_instance_oracle, oracle_pool_map, rel, round_input, sample_points
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -83,24 +83,49 @@ def test_batched_matches_oracle_and_single_apply(precision):
             p.close()
 
 
-def test_batched_config_64_uneven_instances():
+_BATCH64_REF = {}
+
+
+def _batch64_oracle(insts):
+    """Per instance: 8 corners + 8 seeded random points and the FP64 oracle's
+    direct sum there (computed once for the module, in spawned workers)."""
+    if not _BATCH64_REF:
+        jobs = [(it["n"], it["kh"], it["nrhs"], it["x_seed"], sample_points(it["n"], 8, seed=100 + i))
+                for i, it in enumerate(insts)]
+        refs = oracle_pool_map(batched_instance_oracle, jobs)
+        for i, (job, ref) in enumerate(zip(jobs, refs)):
+            _BATCH64_REF[i] = (job[4], ref)
+    return _BATCH64_REF
+
+
+@pytest.mark.parametrize("mode", ["tuned", "persistent"])
+def test_batched_config_64_uneven_instances(mode, monkeypatch):
     """64 instances, each dim from {24,32,48,60,64,84,96}, kh ~ U[2pi/30, 2pi/10],
-    1..16 right-hand sides, complex64: every instance equals its own apply."""
+    1..16 right-hand sides, complex64.  Every instance is checked against the
+    FP64 oracle's direct sum (Sec. I definition) at its 8 corners and 8
+    random points, over all its right-hand sides and components, and against
+    its own btmv_apply (alone vs in the mix).  "tuned" runs the autotuner's
+    choice, "persistent" forces the one-persistent-kernel mode."""
+    if mode == "persistent":
+        monkeypatch.setenv("BTMV_NO_AUTOTUNE", "1")
+        monkeypatch.setenv("BTMV_BATCH_MODE", "0")
     insts = W.batched_instances()
     plans, xs, ys, refs_in = make_batch(insts)
     try:
         out = run_batch(plans, xs, ys)
+        if mode == "persistent":
+            cfg = bt.btmv_batch_tuning([p.handle for p in plans], xs, ys, [x.shape[0] for x in xs])
+            assert cfg["mode"] == 0
+        oracle = _batch64_oracle(insts)
         for i, (p, x, y) in enumerate(zip(plans, xs, out)):
             ya = torch.zeros_like(x)
             p.apply(x, ya, x.shape[0])
             torch.cuda.synchronize()
             assert rel(y, ya.cpu().numpy().astype(np.complex128)) <= 1e-5, i
-        # the two smallest instances against the FP64 oracle as well
-        order = sorted(range(len(insts)), key=lambda i: np.prod(insts[i]["n"]) * insts[i]["nrhs"])
-        for i in order[:2]:
-            t_orth, par, xh = refs_in[i]
-            ref = OE.embed_matvec(W.orthant_to_full(t_orth, par), round_input(xh, 0))
-            assert rel(out[i], ref) <= 1e-5
+            pts, ref = oracle[i]
+            got = np.stack([y[(slice(None), slice(None)) + q] for q in pts])
+            err = rel(got, ref)
+            assert err <= 1e-5, (i, insts[i]["n"], insts[i]["nrhs"], err)
     finally:
         for p in plans:
             p.close()
@@ -163,9 +188,10 @@ def test_persistent_wait_limit_reports_timeout_and_context_survives():
 
 @pytest.mark.parametrize("mode", ["persistent", "branches", "direct"])
 def test_each_batched_execution_mode(mode, monkeypatch):
-    """Every execution mode of btmv_apply_batched gives each problem's own
-    result: the persistent kernel (tuning off), the graph of branches, and
-    the direct stream fork used by the server."""
+    """Every execution mode of btmv_apply_batched matches the FP64 oracle
+    (circulant embedding) and each problem's own apply: the persistent kernel
+    (tuning off), the graph of branches, and the direct stream fork used by
+    the server."""
     if mode in ("persistent", "branches"):
         monkeypatch.setenv("BTMV_NO_AUTOTUNE", "1")
         monkeypatch.setenv("BTMV_BATCH_MODE", "0" if mode == "persistent" else "1")
@@ -175,11 +201,13 @@ def test_each_batched_execution_mode(mode, monkeypatch):
     plans, xs, ys, refs_in = make_batch(insts)
     try:
         out = run_batch(plans, xs, ys)
-        for p, x, y in zip(plans, xs, out):
+        for p, x, y, (t_orth, par, xh) in zip(plans, xs, out, refs_in):
+            ref = OE.embed_matvec(W.orthant_to_full(t_orth, par), round_input(xh, 0))
+            assert rel(y, ref) <= 1e-5                                          # FP64 oracle
             ya = torch.zeros_like(x)
             p.apply(x, ya, x.shape[0])
             torch.cuda.synchronize()
-            assert rel(y, ya.cpu().numpy().astype(np.complex128)) <= 1e-5
+            assert rel(y, ya.cpu().numpy().astype(np.complex128)) <= 1e-5     # alone vs in the mix
         if mode != "direct":
             cfg = bt.btmv_batch_tuning([p.handle for p in plans], xs, ys, [x.shape[0] for x in xs])
             assert cfg["mode"] == (0 if mode == "persistent" else 1)
