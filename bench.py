@@ -2,10 +2,15 @@
 """Block Toeplitz matvec benchmark on GB300: split FFT (Algorithm 1) vs the
 plain full circulant embedding.
 
-Default workload: d = 3, 128^3 grid, c = 3 dyadic Green blocks
+Default workload: d = 3, 256^3 grid, c = 3 dyadic Green blocks
 (kh = 2 pi / 20, fully symmetric, mirror-compressed symbol), complex64, one
-right-hand side.  One step = one btmv_apply (every pass of the path) on
-device-resident inputs.  Prints ONE JSON line on rank 0.
+right-hand side: the largest single-GPU configuration, on which the split
+form is compared with the plain 512^3 full embedding (own kernels and
+cuFFT).  One step = one btmv_apply (every pass of the path) on
+device-resident inputs.  Prints ONE JSON line on rank 0; with the default
+workload the line also carries compact figures of the other workloads
+(128^3 Green, 256^3 skew, 64^2 complex128, batched64, serving200) under
+"secondary" (skip them with --no-secondary).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,11 +38,15 @@ import numpy as np  # noqa: E402
 
 import workloads as W  # noqa: E402
 
-WORKLOAD = "d3_128_c3_green_c64"
-PROFILE_EVERY = 50      # applies per event-profiled apply in the timed region
-CHUNK = 50              # timed-region steps per chunk for the per-step percentiles
+WORKLOAD = "d3_256_c3_green_c64"
+PROFILE_EVERY = 10      # applies per event-profiled apply in the timed region
 L2_BYTES = 129 * 1024 * 1024
-METRIC = "block Toeplitz matvecs/s (split FFT, d=3 128^3 c=3 Green, complex64)"
+
+
+def chunk_steps(steps: int) -> int:
+    """Timed-region steps per chunk for the per-step percentiles: at least
+    ten chunks whenever there are at least ten steps."""
+    return max(1, steps // 10)
 
 
 def metric_name(cfg) -> str:
@@ -59,6 +68,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS) + ["batched64", "serving200", "multirhs"])
     ap.add_argument("--no-compare", action="store_true", help="skip the full-embedding and cuFFT rows")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the compact figures of the other workloads")
     return ap.parse_args()
 
 
@@ -248,12 +259,12 @@ def run_reference(args, cfg):
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
-    if args.workload == "batched64":
-        return run_batched(args)
-    if args.workload == "serving200":
-        return run_serving(args)
-    if args.workload == "multirhs":
-        return run_multirhs(args)
+    if args.workload in ("batched64", "serving200", "multirhs"):
+        fn = {"batched64": run_batched, "serving200": run_serving, "multirhs": run_multirhs}[args.workload]
+        line = fn(args)
+        if line is not None:
+            print(json.dumps(line))
+        return
     cfg = W.WORKLOADS[args.workload]
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
@@ -261,12 +272,24 @@ def main():
         run_reference(args, cfg)
         return
 
+    ws, rank, local = dist_setup(args)
+    line = measure_single(args, cfg, ws, rank, local)
+    if rank == 0 and args.workload == WORKLOAD and not args.no_secondary:
+        line["secondary"] = secondaries(args)
+    barrier(ws)
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def measure_single(args, cfg, ws, rank, local):
+    """The timed split applies of one single-problem workload, with its
+    roofline, end-to-end, CPU-oracle and full-embedding figures; returns the
+    JSON line (rank 0) or None."""
     import torch
 
     from paper_2406_17981_gb300 import analysis as A
     from paper_2406_17981_gb300 import btmv as bt
 
-    ws, rank, local = dist_setup(args)
     n, c = cfg["n"], cfg["c"]
     prec = bt.BTMV_C64 if cfg["precision"] == "c64" else bt.BTMV_C128
     cdt = torch.complex64 if prec == bt.BTMV_C64 else torch.complex128
@@ -278,19 +301,25 @@ def main():
     # kernel durations come from CUDA events recorded live in the timed
     # region around the launches of one apply in every PROFILE_EVERY (events
     # separate launches, so recording every apply would slow the step)
+    V = int(np.prod(n)) * c * esz
+    # rotate over a pool of inputs/outputs so that no step finds its x in L2
+    npool = max(2, math.ceil(2 * L2_BYTES / (2 * V)) + 1)
+    xs = [torch.from_numpy(xc).to("cuda") for _ in range(npool)]
+    ys = [torch.empty_like(xs[0]) for _ in range(npool)]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     os.environ["BTMV_PROFILE_EVERY"] = str(PROFILE_EVERY)
     plan = bt.Plan(n, c, prec, bt.BTMV_ALGO_SPLIT, max_rhs=1, flags=bt.BTMV_FLAG_PROFILE)
     del os.environ["BTMV_PROFILE_EVERY"]
     plan.set_kernel(t, sflags, par)
     info = plan.info
-    V = info["vector_bytes"]
-    # rotate over a pool of inputs/outputs so that no step finds its x in L2
-    npool = max(2, math.ceil(2 * L2_BYTES / (2 * V)) + 1)
-    xs = [torch.from_numpy(xc).to("cuda") for _ in range(npool)]
-    ys = [torch.empty_like(xs[0]) for _ in range(npool)]
+    assert V == info["vector_bytes"]
     for i in range(args.warmup):
         plan.apply(xs[i % npool], ys[i % npool], 1)
     torch.cuda.synchronize()
+    # device memory the plan holds (symbol, tables, workspace), measured
+    plan_resident = free0 - torch.cuda.mem_get_info()[0]
+    CHUNK = chunk_steps(args.steps)
     bt.btmv_profile_read(plan.handle)
     sampler = ClockSampler(local)
     sampler.start()
@@ -396,20 +425,29 @@ def main():
                 got = np.stack([y_gpu[(0, slice(None)) + p] for p in pts])
                 extra["rel_l2_vs_fp64_oracle_sampled"] = float(np.linalg.norm(got - vals[:, 0]) /
                                                                 np.linalg.norm(vals[:, 0]))
-        extra["peak_hbm_split_bytes"] = info["symbol_bytes"] + info["workspace_bytes"] + info["table_bytes"] + 2 * V
+        # peak HBM of one apply: what the plan holds (measured by the drop in
+        # free device memory) plus the caller's x and y
+        extra["peak_hbm_split_bytes"] = plan_resident + 2 * V
+        extra["peak_hbm_split_model_bytes"] = (info["symbol_bytes"] + info["workspace_bytes"] +
+                                               info["table_bytes"] + 2 * V)
         if not args.no_compare:
             extra["two_stream_variant"] = time_two_streams(args, cfg, t, par, sflags, xc, prec, V)
             extra.update(compare_full(args, cfg, t, par, sflags, xc, prec, cdt, V, esz, info))
             full = extra["full_embedding_own"]
             extra["speedup_split_vs_full_own"] = full["ms_per_step"] / (ms_max / args.steps)
+            algo_full = full["algo_bytes_per_step"]
+            extra["byte_ratio_full_own_over_split"] = algo_full / pb["total"]
             extra["peak_hbm_ratio_full_over_split"] = full["peak_hbm_bytes"] / extra["peak_hbm_split_bytes"]
+            extra["peak_hbm_like_for_like"] = like_for_like_memory(args, cfg, t, par, sflags, prec, V, n, c,
+                                                                   extra["peak_hbm_split_bytes"],
+                                                                   full["peak_hbm_bytes"])
             cf = extra.get("full_embedding_cufft", {})
             if "ms_per_step" in cf:
                 extra["speedup_split_vs_cufft_full"] = cf["ms_per_step"] / (ms_max / args.steps)
     del plan
     barrier(ws)
     if rank != 0:
-        return
+        return None
     line = {
         "metric": metric_name(cfg), "value": value, "unit": "matvecs/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -435,19 +473,137 @@ def main():
         "clocks": clocks,
     }
     line.update(extra)
-    print(json.dumps(line))
+    return line
 
 
-def run_batched(args):
-    """64 uneven d=3 Green instances (each dim from {24..96}, 1..16 rhs,
-    complex64) through btmv_apply_batched: one graph replay per step (a
-    persistent kernel or parallel per-instance branches, as tuned).  Rate
-    counts (instance, rhs) pairs."""
+def compact_single(args, workload, steps):
+    """One single-problem workload in brief: split matvecs/s over `steps`
+    applies (inputs rotated past L2), the dominant kernel's roofline, and the
+    error against the FP64 oracle (the full circulant embedding up to 128^3,
+    the direct sum at 8 sampled points above, the dense direct sum for the
+    64^2 complex128 configuration)."""
     import torch
 
     from paper_2406_17981_gb300 import analysis as A
     from paper_2406_17981_gb300 import btmv as bt
-    ws, rank, local = dist_setup(args)
+    cfg = W.WORKLOADS[workload]
+    n, c = cfg["n"], cfg["c"]
+    prec = bt.BTMV_C64 if cfg["precision"] == "c64" else bt.BTMV_C128
+    esz = 8 if prec == bt.BTMV_C64 else 16
+    t, par, sflags = make_generator(cfg)
+    xc = W.random_vector(n, c, seed=cfg["x_seed"]).astype(np.complex64 if esz == 8 else np.complex128)
+    V = int(np.prod(n)) * c * esz
+    npool = max(2, math.ceil(2 * L2_BYTES / (2 * V)) + 1)
+    xs = [torch.from_numpy(xc).cuda() for _ in range(npool)]
+    ys = [torch.empty_like(xs[0]) for _ in range(npool)]
+    os.environ["BTMV_PROFILE_EVERY"] = "5"
+    plan = bt.Plan(n, c, prec, bt.BTMV_ALGO_SPLIT, max_rhs=1, flags=bt.BTMV_FLAG_PROFILE)
+    del os.environ["BTMV_PROFILE_EVERY"]
+    plan.set_kernel(t, sflags, par)
+    info = plan.info
+    for i in range(5):
+        plan.apply(xs[i % npool], ys[i % npool], 1)
+    torch.cuda.synchronize()
+    bt.btmv_profile_read(plan.handle)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(steps):
+        plan.apply(xs[i % npool], ys[i % npool], 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = bt.btmv_profile_read(plan.handle)
+    sampled = (steps + 4) // 5
+    pb = A.split_pass_bytes(n, c, 1, esz, info["symbol_bytes"])
+    kind_bytes = {"fwd_split": pb["fwd_split"], "leaf": pb["leaf"], "merge": pb["bwd_merge"]}
+    peak = float(measured_peaks()[0]["hbm_gbs"])
+    kernels = {}
+    for k, b in kind_bytes.items():
+        if prof[k][1] > 0:
+            per = b / (prof[k][1] / sampled)
+            us = 1000 * prof[k][0] / prof[k][1]
+            kernels[k] = {"avg_us": us, "algo_GBps": per / us / 1e3, "frac": per / us / 1e3 / peak,
+                          "share": prof[k][0] / max(1e-12, sum(v[0] for v in prof.values()))}
+    out = {"matvecs_per_s": 1000.0 / ms, "ms_per_step": ms, "steps": steps,
+           "whole_step_algo_GBps": pb["total"] / ms / 1e6, "whole_step_frac": pb["total"] / ms / 1e6 / peak,
+           "kernels": kernels, "launches_per_step": info["launches_per_apply"]}
+    y = ys[(steps - 1) % npool].cpu().numpy().astype(np.complex128)
+    plan.close()
+    if not args.no_cpu:
+        tf = W.orthant_to_full(t, par) if par is not None else t
+        x128 = xc.astype(np.complex128)
+        if int(np.prod(n)) <= 64 * 64:
+            from oracle import toeplitz as OT
+            ref = OT.direct_matvec(tf, x128)
+            out["rel_l2_vs_fp64_direct_sum"] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+        elif int(np.prod(n)) <= 128 ** 3:
+            from oracle import embed as OE
+            ref = OE.embed_matvec(tf, x128, workers=len(os.sched_getaffinity(0)))
+            out["rel_l2_vs_fp64_oracle"] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+        else:
+            from oracle import toeplitz as OT
+            rng = np.random.default_rng(29)
+            pts = [tuple(int(v) for v in rng.integers(0, n)) for _ in range(8)]
+            vals = OT.direct_points(tf, x128, pts)
+            got = np.stack([y[(0, slice(None)) + q] for q in pts])
+            out["rel_l2_vs_fp64_oracle_sampled"] = float(np.linalg.norm(got - vals[:, 0]) /
+                                                         np.linalg.norm(vals[:, 0]))
+    return out
+
+
+def secondaries(args):
+    """Compact figures of the other configurations, measured after the
+    headline's timed region (each in its own try: a failure is reported, the
+    headline line still prints)."""
+    import torch
+
+    from paper_2406_17981_gb300 import btmv as bt
+    out = {}
+    steps = max(20, min(args.steps, 200))
+    for wl in ("d3_128_c3_green_c64", "d3_256_c3_skew_c64", "d2_64_c1_random_c128"):
+        t0 = time.perf_counter()
+        try:
+            out[wl] = compact_single(args, wl, steps)
+        except Exception as ex:
+            out[wl] = {"error": str(ex)[:300]}
+        out[wl]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    try:
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup = max(10, min(args.steps, 50)), 3
+        b = run_batched(sub, dist=False)
+        out["batched64"] = {k: b[k] for k in ("value", "unit", "ms_per_step")}
+        out["batched64"].update({"mode": b["config"]["launch"], "roofline_frac_whole_step": b["roofline"]["frac"],
+                                 "persistent_kernel_mode": b["persistent_kernel_mode"],
+                                 "sequential_btmv_apply": b["sequential_btmv_apply"]})
+    except Exception as ex:
+        out["batched64"] = {"error": str(ex)[:300]}
+    out["batched64"]["wall_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    try:
+        sv = run_serving(argparse.Namespace(**vars(args)), dist=False)
+        out["serving200"] = {"matvecs_per_s": sv["value"], "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"],
+                             "speedup_vs_one_at_a_time_full": sv["speedup_vs_one_at_a_time_full"],
+                             "matvecs": sv["steps"]}
+    except Exception as ex:
+        out["serving200"] = {"error": str(ex)[:300]}
+    out["serving200"]["wall_s"] = time.perf_counter() - t0
+    del bt
+    return out
+
+
+def run_batched(args, dist=True):
+    """64 uneven d=3 Green instances (each dim from {24..96}, 1..16 rhs,
+    complex64) through btmv_apply_batched: one graph replay per step (a
+    persistent kernel or parallel per-instance branches, as tuned).  Rate
+    counts (instance, rhs) pairs.  Returns the JSON line (rank 0)."""
+    import torch
+
+    from paper_2406_17981_gb300 import analysis as A
+    from paper_2406_17981_gb300 import btmv as bt
+    ws, rank, local = dist_setup(args) if dist else (1, 0, torch.cuda.current_device())
     insts = W.batched_instances()
     plans, xs, ys = [], [], []
     tot_bytes = 0
@@ -519,7 +675,7 @@ def run_batched(args):
     for p in plans:
         p.close()
     if rank != 0:
-        return
+        return None
     line = {"metric": "batched block Toeplitz matvecs/s ((instance, rhs) pairs, 64 uneven d=3 c=3 Green, complex64)",
             "value": value, "unit": "matvecs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -539,7 +695,7 @@ def run_batched(args):
             "persistent_kernel_mode": {"ms_per_step": pers_ms, "matvecs_per_s": pairs / (pers_ms / 1000.0),
                                        "stages": pers_stages},
             "gpu_launches": args.steps * (1 if tuning["mode"] == 0 else tuning["stages"]), "clocks": clocks}
-    print(json.dumps(line))
+    return line
 
 
 def run_multirhs(args):
@@ -586,13 +742,13 @@ def run_multirhs(args):
             out[f"{n[0]}^3 r16 {name}"]["rel_diff_vs_register"] = float(
                 np.linalg.norm(ys[name] - ref) / np.linalg.norm(ref))
     if rank != 0:
-        return
+        return None
     best = max(v["rhs_matvecs_per_s"] for k, v in out.items() if k.startswith("128"))
     line = {"metric": "multi-rhs block Toeplitz rhs-matvecs/s (d=3 c=3 Green, 16 rhs, complex64)",
             "value": best, "unit": "matvecs/s", "n_gpus": ws, "steps": steps, "warmup": 3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": {"workload": "multirhs", "nrhs": 16}, "variants": out}
-    print(json.dumps(line))
+    return line
 
 
 def serving_specs(count=200, seed=7):
@@ -627,15 +783,15 @@ def serving_specs(count=200, seed=7):
     return specs
 
 
-def run_serving(args):
+def run_serving(args, dist=True):
     """Serving: continuous batching of the matvecs of 200 concurrent solves
     (80 GB HBM budget), against the same solves one matvec at a time with
-    the plain full embedding."""
+    the plain full embedding.  Returns the JSON line (rank 0)."""
     import torch
 
     from paper_2406_17981_gb300 import btmv as bt
     from paper_2406_17981_gb300 import serve
-    ws, rank, local = dist_setup(args)
+    ws, rank, local = dist_setup(args) if dist else (1, 0, torch.cuda.current_device())
     t0 = time.perf_counter()
     specs = serving_specs()
     t_setup = time.perf_counter() - t0
@@ -653,7 +809,7 @@ def run_serving(args):
     base = serve.Server(budget_bytes=80 * 10 ** 9, max_inflight=1, algo=bt.BTMV_ALGO_FULL,
                         batched=False).run(specs)
     if rank != 0:
-        return
+        return None
     strip = lambda r: {k: v for k, v in r.items() if k not in ("solutions", "rhs")}  # noqa: E731
     line = {"metric": "served block Toeplitz matvecs/s (200 concurrent BiCGSTAB solves, complex64)",
             "value": res["matvecs_per_s"], "unit": "matvecs/s", "n_gpus": ws, "steps": res["matvecs"],
@@ -667,7 +823,7 @@ def run_serving(args):
             "p50_ms": res["p50_ms"], "p99_ms": res["p99_ms"],
             "speedup_vs_one_at_a_time_full": res["matvecs_per_s"] / base["matvecs_per_s"],
             "clocks": clocks}
-    print(json.dumps(line))
+    return line
 
 
 def time_two_streams(args, cfg, t, par, sflags, xc, prec, V):
@@ -703,8 +859,28 @@ def time_two_streams(args, cfg, t, par, sflags, xc, prec, V):
             "peak_hbm_bytes": info["symbol_bytes"] + info["workspace_bytes"] + info["table_bytes"] + 2 * V}
 
 
+def time_plan_apply(plan, x, y, steps):
+    """Mean ms of `steps` applies on device buffers (after 3 warm-up applies)."""
+    import torch
+    for _ in range(3):
+        plan.apply(x, y, 1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.apply(x, y, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
 def compare_full(args, cfg, t, par, sflags, xc, prec, cdt, V, esz, info_split):
-    """The plain full embedding: own kernels, and cuFFT through torch.fft."""
+    """The plain full embedding (Sec. I) on the same symbol store as the split
+    plan: with the library's own kernels, and with cuFFT transforms
+    (BTMV_ALGO_FULL_CUFFT: cuFFT plus the library's pad, multiply and
+    projection kernels).  Peak HBM = device memory the plan holds (measured
+    as the drop in free memory, cuFFT's work area included) + x and y."""
     import torch
 
     from paper_2406_17981_gb300 import analysis as A
@@ -712,86 +888,51 @@ def compare_full(args, cfg, t, par, sflags, xc, prec, cdt, V, esz, info_split):
     n, c = cfg["n"], cfg["c"]
     out = {}
     steps = max(10, min(args.steps, 200))
-    fp = bt.Plan(n, c, prec, bt.BTMV_ALGO_FULL, max_rhs=1, flags=bt.BTMV_FLAG_PROFILE)
-    fp.set_kernel(t, sflags, par)
-    finfo = fp.info
-    sym_store = bt.btmv_get_symbol(fp.handle)
     x = torch.from_numpy(xc).cuda()
     y = torch.empty_like(x)
-    for _ in range(3):
-        fp.apply(x, y, 1)
-    torch.cuda.synchronize()
-    bt.btmv_profile_read(fp.handle)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        fp.apply(x, y, 1)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    fb = A.full_pass_bytes(n, c, 1, esz, finfo["symbol_bytes"])
-    out["full_embedding_own"] = {
-        "matvecs_per_s": 1000.0 / ms, "ms_per_step": ms,
-        "algo_bytes_per_step": fb["total"], "algo_GBps": fb["total"] / (ms / 1000) / 1e9,
-        "peak_hbm_bytes": finfo["symbol_bytes"] + finfo["workspace_bytes"] + finfo["table_bytes"] + 2 * V}
-    del fp
-    torch.cuda.synchronize()
-    # cuFFT (torch.fft) plain embedding; its symbol is the library's own FP64
-    # build of the full 2n-grid store, interleaved back from its parity classes
-    try:
-        Sfull = torch.from_numpy(full_symbol_grid(sym_store, finfo, n, c)).cuda()
-        torch.cuda.reset_peak_memory_stats()
-        base = torch.cuda.memory_allocated()
-        big = tuple(2 * m for m in n)
-        scale = float(np.prod(big))
-
-        def step():
-            xp = torch.zeros((1, c) + big, dtype=cdt, device="cuda")
-            xp[(slice(None), slice(None)) + tuple(slice(0, m) for m in n)] = x
-            X = torch.fft.fftn(xp, dim=(2, 3, 4)[:len(n)])
-            Y = torch.stack([sum(Sfull[a_, b_] * X[:, b_] for b_ in range(c)) for a_ in range(c)], dim=1) * scale
-            yy = torch.fft.ifftn(Y, dim=(2, 3, 4)[:len(n)])
-            return yy[(slice(None), slice(None)) + tuple(slice(0, m) for m in n)].contiguous()
-
-        for _ in range(3):
-            step()
-        torch.cuda.synchronize()
-        csteps = max(5, min(args.steps, 50))
-        e0.record()
-        for _ in range(csteps):
-            step()
-        e1.record()
-        torch.cuda.synchronize()
-        cms = e0.elapsed_time(e1) / csteps
-        out["full_embedding_cufft"] = {"matvecs_per_s": 1000.0 / cms, "ms_per_step": cms,
-                                       "peak_hbm_bytes": torch.cuda.max_memory_allocated() - base
-                                       + Sfull.numel() * Sfull.element_size()}
-        del Sfull
-    except Exception as ex:  # report, never fail the bench line
-        out["full_embedding_cufft"] = {"error": str(ex)[:200]}
+    for key, algo in (("full_embedding_own", bt.BTMV_ALGO_FULL), ("full_embedding_cufft", bt.BTMV_ALGO_FULL_CUFFT)):
+        try:
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
+            fp = bt.Plan(n, c, prec, algo, max_rhs=1)
+            fp.set_kernel(t, sflags, par)
+            finfo = fp.info
+            ms = time_plan_apply(fp, x, y, steps)
+            resident = free0 - torch.cuda.mem_get_info()[0]
+            fb = A.full_pass_bytes(n, c, 1, esz, finfo["symbol_bytes"])
+            out[key] = {"matvecs_per_s": 1000.0 / ms, "ms_per_step": ms,
+                        "symbol": "compressed" if finfo["compressed"] else "full",
+                        "algo_bytes_per_step": fb["total"], "algo_GBps": fb["total"] / (ms / 1000) / 1e9,
+                        "peak_hbm_bytes": resident + 2 * V,
+                        "peak_hbm_model_bytes": (finfo["symbol_bytes"] + finfo["workspace_bytes"] +
+                                                 finfo["table_bytes"] + 2 * V)}
+            if algo == bt.BTMV_ALGO_FULL_CUFFT:
+                out[key]["kernels"] = "cuFFT C2C (cufftPlanMany, c batched) + own pad / multiply / projection"
+            fp.close()
+            del fp
+        except Exception as ex:  # report, never fail the bench line
+            out[key] = {"error": str(ex)[:200]}
     return out
 
 
-def full_symbol_grid(store, info, n, c):
-    """[c][c][2n_1..2n_d] symbol from a full (uncompressed) class-major store:
-    class b holds S[2 j + b] for j < n (the layout btmv_get_symbol documents)."""
+def like_for_like_memory(args, cfg, t, par, sflags, prec, V, n, c, split_peak, full_peak):
+    """Peak-HBM ratio full embedding / split with the same symbol storage on
+    both sides, measured (both on the mirror-compressed store when the
+    workload has parity symmetry), beside the model of Eq. MemRatio /
+    MemRatioSym extended to c x c blocks: symbol S in units of s elements,
+    vectors c per unit; the paper's accounting (embedding in place, split
+    holding x) and this library's (x and y both held by the caller)."""
+    from paper_2406_17981_gb300 import analysis as A
     d = len(n)
-    nsym = info["nsym"]
-    blocks = ([(a, a) for a in range(c)] + [(a, b) for a in range(c) for b in range(a + 1, c)]
-              if nsym == c * (c + 1) // 2 and c > 1 else [(a, b) for a in range(c) for b in range(c)])
-    out = np.zeros((c, c) + tuple(2 * m for m in n), dtype=store.dtype)
     s = int(np.prod(n))
-    off = 0
-    for cls in range(1 << d):
-        bits = [(cls >> (d - 1 - m)) & 1 for m in range(d)]
-        sl = tuple(slice(bits[m], None, 2) for m in range(d))
-        for k in range(nsym):
-            a, b = blocks[k]
-            blk = store[off:off + s].reshape(n)
-            out[(a, b) + sl] = blk
-            out[(b, a) + sl] = blk
-            off += s
+    bsym = bool(sflags & 1)
+    S_comp = A.symbol_bytes(n, c, 1, bsym, True) / s
+    S_full = A.symbol_bytes(n, c, 1, bsym, False) / s
+    out = {"measured_same_store": full_peak / split_peak,
+           "store": "compressed" if sflags & 2 else "full"}
+    for name, S in (("compressed", S_comp), ("full", S_full)):
+        out[f"model_paper_accounting_{name}"] = A.ratio_memory_blocks(d, c, S, S)
+        out[f"model_x_and_y_held_{name}"] = (2 ** d * c + 2 * c + S) / ((d + 1) * c + S)
     return out
 
 

@@ -66,8 +66,12 @@ enum { BTMV_C64 = 0, BTMV_C128 = 1 };
 /* algorithm */
 enum {
   BTMV_ALGO_SPLIT = 0,     /* Algorithm 1: lazy embedding, eager projection      */
-  BTMV_ALGO_FULL = 1       /* plain full 2^d circulant embedding (Sec. I), own
+  BTMV_ALGO_FULL = 1,      /* plain full 2^d circulant embedding (Sec. I), own
                               kernels; for comparison                          */
+  BTMV_ALGO_FULL_CUFFT = 2 /* the same embedding with cuFFT transforms (own pad,
+                              multiply and projection kernels); d <= 3; cuFFT
+                              is loaded at run time (dlopen) by the first such
+                              plan; for comparison only                       */
 };
 
 /* symmetry flags for btmv_set_kernel (may be OR-ed) */
@@ -124,12 +128,14 @@ enum {
  *             operator's symbol).
  *   c         block size (components), 1 <= c <= 3.
  *   precision BTMV_C64 or BTMV_C128.
- *   algo      BTMV_ALGO_SPLIT or BTMV_ALGO_FULL.
+ *   algo      BTMV_ALGO_SPLIT, BTMV_ALGO_FULL or BTMV_ALGO_FULL_CUFFT (as FULL,
+ *             d <= 3; BTMV_E_UNSUPPORTED when libcufft cannot be loaded).
  *   max_rhs   largest nrhs later passed to btmv_apply (>= 1).
  *   flags     BTMV_FLAG_*.
  * Allocates the twiddle tables and the workspace: (d - 1) vectors of
  * max_rhs * c * prod(n) complex for SPLIT (the paper's (d+1)-vector peak with
- * x and y, Sec. II.C), 2^d such vectors for FULL.  The device is the current
+ * x and y, Sec. II.C), 2^d such vectors for FULL and FULL_CUFFT (plus
+ * cuFFT's own work area for FULL_CUFFT).  The device is the current
  * CUDA device.  Errors: BTMV_E_ARG, BTMV_E_UNSUPPORTED, BTMV_E_NOMEM, BTMV_E_CUDA.
  */
 BTMV_API btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n, int c,
@@ -165,9 +171,10 @@ BTMV_API btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flags,
  * (-1)^b c~_hi)) / prod(2 n_m) of the transformed embedded generator
  * (Sec. I embedding with free entry s0 = 0; Sec. II.C split into 2^d parts)
  * and rounds it once to the plan precision.  Storage: full, 2^d prod(n) values
- * per stored block; or with BTMV_SYM_PARITY (split algo only) the mirror-
- * compressed prod(n_m + 1) values per stored block (Sec. II.C symmetric /
- * skew-symmetric storage).  May be called again to replace the generator.
+ * per stored block; or with BTMV_SYM_PARITY the mirror-compressed
+ * prod(n_m + 1) values per stored block (Sec. II.C symmetric /
+ * skew-symmetric storage; both algorithms read it, the plain embedding at
+ * its full-grid frequencies folded by f -> 2n - f).  May be called again to replace the generator.
  * Errors: BTMV_E_ARG, BTMV_E_NOMEM, BTMV_E_CUDA.
  */
 BTMV_API btmv_status btmv_set_kernel(btmv_plan p, const double* t, uint32_t sym_flags,
@@ -266,6 +273,8 @@ BTMV_API btmv_status btmv_host_wait(btmv_plan p);
  * whose contents persist between calls (no call reads what an earlier one
  * left there); calls whose work overlaps on the same GPU (other host threads
  * or streams) race on it and must be serialised by the caller.
+ * The plan's device must be the current device (BTMV_E_ARG otherwise): the
+ * array staged on is the current device's copy.
  * Errors: as btmv_apply, plus BTMV_E_UNSUPPORTED for the size limit.
  */
 #define BTMV_NOALLOC_MAX_BYTES (16u << 20)

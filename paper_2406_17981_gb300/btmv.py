@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "btmv.h")
 
 BTMV_OK, BTMV_E_ARG, BTMV_E_NOMEM, BTMV_E_CUDA, BTMV_E_STATE, BTMV_E_UNSUPPORTED, BTMV_E_TIMEOUT = range(7)
 BTMV_C64, BTMV_C128 = 0, 1
-BTMV_ALGO_SPLIT, BTMV_ALGO_FULL = 0, 1
+BTMV_ALGO_SPLIT, BTMV_ALGO_FULL, BTMV_ALGO_FULL_CUFFT = 0, 1, 2
 BTMV_SYM_NONE, BTMV_SYM_BLOCK, BTMV_SYM_PARITY, BTMV_SYM_ADJOINT = 0, 1, 2, 4
 BTMV_FLAG_NONE, BTMV_FLAG_PROFILE, BTMV_FLAG_GENERIC, BTMV_FLAG_SHARED_RHS, BTMV_FLAG_TENSOR_CORE = 0, 1, 2, 4, 8
 BTMV_FLAG_TWO_STREAMS = 16

@@ -122,6 +122,7 @@ static void set_fft(btmv_plan p, FftDev& f, int N, bool dbl) {
 
 static void free_plan(btmv_plan p) {
   if (!p) return;
+  cufft_plan_destroy(p);
   for (auto& r : p->pending) { p->pool.push_back(r.a); p->pool.push_back(r.b); }
   for (auto e : p->pool) cudaEventDestroy(e);
   p->tab.owner.reset();       // freed with the last plan sharing them
@@ -196,19 +197,22 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
   if (!n) return fail(BTMV_E_ARG, "plan_create: n is NULL");
   if (c < 1 || c > 3) return fail(BTMV_E_ARG, "plan_create: c=%d outside [1,3]", c);
   if (precision != BTMV_C64 && precision != BTMV_C128) return fail(BTMV_E_ARG, "plan_create: bad precision %d", precision);
-  if (algo != BTMV_ALGO_SPLIT && algo != BTMV_ALGO_FULL) return fail(BTMV_E_ARG, "plan_create: bad algo %d", algo);
+  if (algo != BTMV_ALGO_SPLIT && algo != BTMV_ALGO_FULL && algo != BTMV_ALGO_FULL_CUFFT)
+    return fail(BTMV_E_ARG, "plan_create: bad algo %d", algo);
   if (max_rhs < 1) return fail(BTMV_E_ARG, "plan_create: max_rhs=%d < 1", max_rhs);
   if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC | BTMV_FLAG_SHARED_RHS | BTMV_FLAG_TENSOR_CORE |
                           BTMV_FLAG_TWO_STREAMS))
     return fail(BTMV_E_ARG, "plan_create: unknown flags 0x%x", flags);
   if (algo == BTMV_ALGO_FULL && d > 4)
     return fail(BTMV_E_UNSUPPORTED, "plan_create: the plain embedding takes d <= 4 (d=%d)", d);
+  if (algo == BTMV_ALGO_FULL_CUFFT && d > 3)
+    return fail(BTMV_E_UNSUPPORTED, "plan_create: the cuFFT embedding takes d <= 3 (d=%d)", d);
   int np[MAX_D];
   for (int m = 0; m < d; ++m) {
     if (n[m] < 1) return fail(BTMV_E_ARG, "plan_create: n[%d]=%d < 1", m, n[m]);
     if (n[m] > 1024) return fail(BTMV_E_UNSUPPORTED, "plan_create: n[%d]=%d > 1024", m, n[m]);
     FftDev f;
-    if (algo == BTMV_ALGO_FULL) {
+    if (algo != BTMV_ALGO_SPLIT) {
       if (!factor_radices(2 * n[m], f))
         return fail(BTMV_E_UNSUPPORTED, "plan_create: the plain embedding needs 7-smooth sizes (n[%d]=%d)", m, n[m]);
       np[m] = n[m];
@@ -234,14 +238,14 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
 
   std::vector<int> Nf, Nd;
   for (int m = 0; m < d; ++m) {
-    const int N = algo == BTMV_ALGO_FULL ? 2 * n[m] : n[m];
+    const int N = algo != BTMV_ALGO_SPLIT ? 2 * n[m] : n[m];
     if (precision == BTMV_C64) Nf.push_back(N); else Nd.push_back(N);
     Nd.push_back(n[m]);  // FP64 symbol build
   }
   btmv_status st = build_tables(p, Nf, Nd);
   if (st != BTMV_OK) { free_plan(p); return st; }
   for (int m = 0; m < d; ++m) {
-    const int N = algo == BTMV_ALGO_FULL ? 2 * n[m] : n[m];
+    const int N = algo != BTMV_ALGO_SPLIT ? 2 * n[m] : n[m];
     set_fft(p, p->fft_apply[m], N, precision == BTMV_C128);
     set_fft(p, p->fft_sym[m], n[m], true);
   }
@@ -261,6 +265,10 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
   if (st != BTMV_OK) { free_plan(p); return st; }
   st = setup_padding(p, V);
   if (st != BTMV_OK) { free_plan(p); return st; }
+  if (algo == BTMV_ALGO_FULL_CUFFT) {
+    st = cufft_plan_setup(p);
+    if (st != BTMV_OK) { free_plan(p); return st; }
+  }
   read_profile_every(p);
   *out = p;
   return BTMV_OK;
@@ -296,8 +304,12 @@ extern "C" btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flag
       p->W.push_back(p->ws);
   }
   {
-    const btmv_status st = setup_padding(p, V);
+    btmv_status st = setup_padding(p, V);
     if (st != BTMV_OK) { free_plan(p); return st; }
+    if (p->algo == BTMV_ALGO_FULL_CUFFT) {
+      st = cufft_plan_setup(p);
+      if (st != BTMV_OK) { free_plan(p); return st; }
+    }
   }
   read_profile_every(p);
   *out = p;
@@ -428,7 +440,9 @@ extern "C" btmv_status btmv_set_kernel(btmv_plan p, const double* t, uint32_t sy
   }
   cudaStream_t st = (cudaStream_t)stream;
   const int nsym = bsym ? c * (c + 1) / 2 : c * c;
-  const int compressed = (par && p->algo == BTMV_ALGO_SPLIT) ? 1 : 0;
+  // the mirror-compressed store serves both algorithms: the plain embedding's
+  // leaf reads its full-grid frequencies f_m in [0, 2 n_m) folded to 2 n_m - f_m
+  const int compressed = par ? 1 : 0;
 
   // class geometry
   SymDev sd;
@@ -925,6 +939,10 @@ static btmv_status apply_device(btmv_plan p, const void* x, void* y, int nrhs, c
   }
   if (p->algo == BTMV_ALGO_SPLIT)
     return c64 ? split_apply<float2>(p, x, y, nrhs, st) : split_apply<double2>(p, x, y, nrhs, st);
+  if (p->algo == BTMV_ALGO_FULL_CUFFT) {
+    ProfScope ps(p, BTMV_K_FULL_LEAF, st);
+    return cufft_full_apply(p, x, y, nrhs, st);
+  }
   return c64 ? full_apply<float2>(p, x, y, nrhs, st) : full_apply<double2>(p, x, y, nrhs, st);
 }
 
@@ -953,6 +971,8 @@ btmv_status btmv_apply_on_device(btmv_plan p, const void* x, void* y, int nrhs, 
   return apply_device(p, x, y, nrhs, st);
 }
 btmv_status btmv_set_error(btmv_status st, const char* msg) { return fail(st, "%s", msg); }
+void btmv_clear_error() { g_err.clear(); }
+int btmv_plan_device(btmv_plan p) { return p->dev; }
 int btmv_is_device_ptr(const void* ptr) { return is_device_ptr(ptr); }
 
 extern "C" btmv_status btmv_apply(btmv_plan p, const void* x, void* y, int nrhs, void* stream) {
@@ -1006,6 +1026,7 @@ static int launches_per_apply(btmv_plan p) {
     n += 1 << (d - 2);
     return n;
   }
+  if (p->algo == BTMV_ALGO_FULL_CUFFT) return 3;   // pad, multiply, projection (+ cuFFT's own kernels)
   if (d == 1) return 3;
   return 2 * (d - 2) + 3;
 }

@@ -68,6 +68,9 @@ struct btmv_plan_s {
   std::vector<void*> W2;
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // BTMV_ALGO_FULL_CUFFT: the cuFFT plan (cufftHandle) of one right-hand side
+  int cufft = 0;
+  bool has_cufft = false;
   // host staging
   void* stage_x = nullptr;
   void* stage_y = nullptr;
@@ -117,5 +120,9 @@ PassArgs split_pass_args(btmv_plan p, const Step& s, int nrhs, size_t esz, int T
 LeafArgs leaf_step_args(btmv_plan p, int nrhs, int nn, const LeafNode* nodes, bool full, size_t esz, int Lt, int rq);
 // Drop every cached batch that refers to plan p (called by btmv_destroy).
 void batch_forget_plan(btmv_plan p);
+// BTMV_ALGO_FULL_CUFFT (cufft_full.cu): cuFFT plan set-up / release, apply.
+btmv_status cufft_plan_setup(btmv_plan p);
+void cufft_plan_destroy(btmv_plan p);
+btmv_status cufft_full_apply(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st);
 
 }  // namespace btmv

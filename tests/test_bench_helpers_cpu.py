@@ -6,7 +6,10 @@ import workloads as W
 
 
 def test_metric_names():
-    assert bench.metric_name(W.WORKLOADS["d3_128_c3_green_c64"]) == bench.METRIC
+    assert bench.WORKLOAD == "d3_256_c3_green_c64"
+    assert bench.metric_name(W.WORKLOADS[bench.WORKLOAD]) == \
+        "block Toeplitz matvecs/s (split FFT, d=3 256^3 c=3 Green, complex64)"
+    assert "128^3" in bench.metric_name(W.WORKLOADS["d3_128_c3_green_c64"])
     assert "256^3" in bench.metric_name(W.WORKLOADS["d3_256_c3_skew_c64"])
     assert "complex128" in bench.metric_name(W.WORKLOADS["d2_64_c1_random_c128"])
 
@@ -27,3 +30,9 @@ def test_ncu_traffic_follows_the_kernel_sources(monkeypatch):
 def test_source_sha_depends_on_the_kind():
     assert bench.source_sha("leaf") != bench.source_sha("fwd_split")
     assert len(bench.source_sha()) == 16
+
+
+def test_chunks_give_percentiles_at_the_driver_step_counts():
+    for steps in (10, 20, 50, 1000):
+        assert steps // bench.chunk_steps(steps) >= 10
+    assert bench.chunk_steps(3) == 1

@@ -201,6 +201,70 @@ def test_register_kernels_vs_oracle_and_generic(n, c, algo):
     assert rel(y, yg) <= 2e-6
 
 
+FULL_COMPRESSED = [((12, 10, 8), 3, "green"), ((16, 32, 64), 3, "green"), ((5, 7, 9), 3, "green"),
+                   ((96, 24, 6), 3, "green"), ((64, 64), 1, "green"), ((24, 96), 1, "green"),
+                   ((6, 10), 3, "skew"), ((8, 6, 4), 3, "skew")]
+
+
+@pytest.mark.parametrize("n,c,kind", FULL_COMPRESSED)
+@pytest.mark.parametrize("generic", [False, True])
+def test_full_embedding_reads_the_compressed_store(n, c, kind, generic):
+    """The plain embedding on the mirror-compressed store (Sec. II.C
+    symmetric / skew storage): its full-grid frequencies f > n are read at
+    2n - f with the block's parity sign."""
+    if kind == "skew":
+        t_orth, par = W.skew_orthant(n, seed=71, c=c)
+    elif c == 3:
+        t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    else:
+        t_orth, par = W.green_scalar_orthant(n, kh=W.KH_GREEN)
+    flags = bt.BTMV_SYM_PARITY | (bt.BTMV_SYM_BLOCK if c == 3 else 0)
+    x = W.random_vector(n, c, seed=72, nrhs=2)
+    tf = W.orthant_to_full(t_orth, par)
+    for precision in (0, 1):
+        plan = bt.Plan(n, c, precision, bt.BTMV_ALGO_FULL, max_rhs=2,
+                       flags=bt.BTMV_FLAG_GENERIC if generic else 0)
+        try:
+            plan.set_kernel(t_orth, flags, par)
+            assert plan.info["compressed"] == 1
+            dt = torch.complex64 if precision == 0 else torch.complex128
+            xd = torch.from_numpy(x).to(dt).cuda()
+            yd = torch.zeros_like(xd)
+            plan.apply(xd, yd, 2)
+            torch.cuda.synchronize()
+        finally:
+            plan.close()
+        ref = OE.embed_matvec(tf, round_input(x, precision))
+        assert rel(yd.cpu().numpy().astype(np.complex128), ref) <= TOL[precision]
+
+
+CUFFT_CASES = [((32,), 1, "random"), ((64, 64), 1, "random"), ((6, 5, 4), 3, "random"), ((12, 10, 8), 3, "green"),
+               ((16, 32, 64), 3, "green"), ((8, 6, 4), 3, "skew"), ((24, 96), 1, "green")]
+
+
+@pytest.mark.parametrize("n,c,kind", CUFFT_CASES)
+def test_cufft_embedding_vs_oracle(n, c, kind):
+    """BTMV_ALGO_FULL_CUFFT (the comparator: cuFFT transforms, own pad,
+    multiply and projection kernels) on the full and the compressed store."""
+    if kind == "random":
+        t_in, par, flags = W.random_generator(n, c, seed=81), None, 0
+        tf = t_in
+    else:
+        if kind == "skew":
+            t_in, par = W.skew_orthant(n, seed=82, c=c)
+        elif c == 3:
+            t_in, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+        else:
+            t_in, par = W.green_scalar_orthant(n, kh=W.KH_GREEN)
+        flags = bt.BTMV_SYM_PARITY | (bt.BTMV_SYM_BLOCK if c == 3 else 0)
+        tf = W.orthant_to_full(t_in, par)
+    x = W.random_vector(n, c, seed=83, nrhs=2)
+    for precision in (0, 1):
+        y = run_btmv(t_in, x, n, c, precision, bt.BTMV_ALGO_FULL_CUFFT, flags, par)
+        ref = OE.embed_matvec(tf, round_input(x, precision))
+        assert rel(y, ref) <= TOL[precision]
+
+
 def test_plan_clone_shares_the_symbol():
     n, c = (10, 12, 8), 3
     t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
