@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS) + ["batched64", "serving200", "multirhs"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS) + ["batched64", "serving200", "multirhs", "cpu_fig3"])
     ap.add_argument("--no-compare", action="store_true", help="skip the full-embedding and cuFFT rows")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
     ap.add_argument("--no-secondary", action="store_true",
@@ -259,8 +259,9 @@ def run_reference(args, cfg):
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
-    if args.workload in ("batched64", "serving200", "multirhs"):
-        fn = {"batched64": run_batched, "serving200": run_serving, "multirhs": run_multirhs}[args.workload]
+    if args.workload in ("batched64", "serving200", "multirhs", "cpu_fig3"):
+        fn = {"batched64": run_batched, "serving200": run_serving, "multirhs": run_multirhs,
+              "cpu_fig3": run_cpu_fig3}[args.workload]
         line = fn(args)
         if line is not None:
             print(json.dumps(line))
@@ -749,6 +750,31 @@ def run_multirhs(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": {"workload": "multirhs", "nrhs": 16}, "variants": out}
     return line
+
+
+def run_cpu_fig3(args):
+    """The paper's wall-clock study (Sec. III, Fig. 3) on the host cores:
+    split vs full circulant embedding, d = 1..4, power-of-two sizes, scalar
+    random complex generators, scipy.fft on every core this process may use.
+    No GPU.  The operation-count ratio R_c (Eq. CompRatio) is printed beside
+    each measured ratio."""
+    from paper_2406_17981_gb300 import analysis as A
+    from paper_2406_17981_gb300 import cpu_study as CS
+    if int(os.environ.get("RANK", "0")) != 0:
+        return None
+    t0 = time.perf_counter()
+    rows = CS.study(repeats=3)
+    for r in rows:
+        r["model_R_c"] = A.ratio_complexity(r["d"], r["n"])
+    el = time.perf_counter() - t0
+    best = max(r["ratio_embed_over_split"] for r in rows)
+    return {"metric": "wall-clock ratio full embedding / split on the host cores (Sec. III study)",
+            "value": best, "unit": "ratio", "n_gpus": 0, "steps": len(rows), "warmup": 1,
+            "ms_per_step": 1000.0 * el / max(1, len(rows)), "higher_is_better": True, "scaling": "none",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cpu_fig3", "cores": CS.cores(), "fft": "scipy.fft",
+                       "sizes": {str(k): v for k, v in CS.DEFAULT_SIZES.items()}},
+            "rows": rows}
 
 
 def serving_specs(count=200, seed=7):

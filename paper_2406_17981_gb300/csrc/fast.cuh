@@ -117,8 +117,17 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 template <class P> __host__ __device__ constexpr int pad_div() { return P::T < 16 ? P::T : 16; }
 template <class P> __host__ __device__ constexpr int padded_len() { return P::N + P::N / pad_div<P>(); }
 
+// Stage twiddle load: from the read-only global table (TWSM = false) or from
+// a copy in shared memory (TWSM = true; a plain load, re-read at every use
+// rather than held in registers across transforms).
+template <bool TWSM>
+__device__ __forceinline__ float2 twld(const float2* __restrict__ tw, int i) {
+  if constexpr (TWSM) return tw[i];
+  else return __ldg(&tw[i]);
+}
+
 // In: a[m] = v[t + T m].  Out: a[m] = DFT(v)[t + T m] (forward or inverse, unnormalised).
-template <class P, bool INV, class SM>
+template <class P, bool INV, class SM, bool TWSM = false>
 __device__ __forceinline__ void fft_reg(float2 (&a)[P::R1], int t, const SM& sm, const float2* __restrict__ tw) {
   constexpr int R1 = P::R1, R2 = P::R2, R3 = P::R3, TT = P::T;
   dft<R1, INV>(a);
@@ -135,7 +144,7 @@ __device__ __forceinline__ void fft_reg(float2 (&a)[P::R1], int t, const SM& sm,
 #pragma unroll
       for (int r = 0; r < R2; ++r) b[r] = sm.ld(f1 * R2 + r);
 #pragma unroll
-      for (int r = 1; r < R2; ++r) b[r] = twm<INV>(b[r], __ldg(&tw[r * f1]));
+      for (int r = 1; r < R2; ++r) b[r] = twm<INV>(b[r], twld<TWSM>(tw, r * f1));
       dft<R2, INV>(b);
 #pragma unroll
       for (int f2 = 0; f2 < R2; ++f2) a[q + NQ * f2] = b[f2];
@@ -151,7 +160,7 @@ __device__ __forceinline__ void fft_reg(float2 (&a)[P::R1], int t, const SM& sm,
 #pragma unroll
       for (int r = 0; r < R2; ++r) c2[q][r] = sm.ld(kp + MP * (R2 * f1 + r));
 #pragma unroll
-      for (int r = 1; r < R2; ++r) c2[q][r] = twm<INV>(c2[q][r], __ldg(&tw[r * f1 * MP]));
+      for (int r = 1; r < R2; ++r) c2[q][r] = twm<INV>(c2[q][r], twld<TWSM>(tw, r * f1 * MP));
       dft<R2, INV>(c2[q]);
     }
     sm.sync();
@@ -170,7 +179,7 @@ __device__ __forceinline__ void fft_reg(float2 (&a)[P::R1], int t, const SM& sm,
 #pragma unroll
       for (int r = 0; r < R3; ++r) b[r] = sm.ld(f1 * R3 + r);
 #pragma unroll
-      for (int r = 1; r < R3; ++r) b[r] = twm<INV>(b[r], __ldg(&tw[r * f1]));
+      for (int r = 1; r < R3; ++r) b[r] = twm<INV>(b[r], twld<TWSM>(tw, r * f1));
       dft<R3, INV>(b);
 #pragma unroll
       for (int f2 = 0; f2 < R3; ++f2) a[q + NQ3 * f2] = b[f2];

@@ -1,5 +1,7 @@
 // Register-resident fused leaf pass for the line lengths fast.cuh provides
 // plans for.
+#include <cstdlib>
+
 #include "fast.cuh"
 
 namespace btmv {
@@ -59,14 +61,20 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
   float2* const phs = smem_cg + CF::LPC * C * CF::GS;           // phase table P (N values)
   const SymDev& S = a.sym;
   constexpr int NS = C == 3 ? 6 : 1;                            // stored blocks staged by FF kernels
-  float2* const rowb = phs + N + li * CF::line_stride(FF ? NS : 0);  // staged symbol row of this line
   const LeafNode nd = a.nodes[blockIdx.y];
-  // 32-bit line arithmetic: the launcher guarantees nrhs * lines < 2^31
+  // 32-bit line arithmetic: the launcher guarantees nrhs * lines < 2^31.
+  // Lines are ordered right-hand side fastest: the lines of one spatial line
+  // for several right-hand sides sit in one block and share one staged
+  // symbol row (slot li0, the block's first line of that spatial line), so
+  // the row is read once for all of them.
   const unsigned lines = (unsigned)a.lines;
-  const unsigned gline = blockIdx.x * (unsigned)CF::LPC + (unsigned)li;   // over (rhs, line)
-  const bool ok = gline < (unsigned)a.nrhs * lines;
-  const unsigned q = ok ? gline / lines : 0u;
-  const unsigned line = ok ? gline - q * lines : 0u;
+  const unsigned nr = (unsigned)a.nrhs;
+  const unsigned gline = blockIdx.x * (unsigned)CF::LPC + (unsigned)li;   // over (line, rhs)
+  const bool ok = gline < nr * lines;
+  const unsigned line = ok ? gline / nr : 0u;
+  const unsigned q = ok ? gline - line * nr : 0u;
+  const int li0 = li - (int)(q < (unsigned)li ? q : (unsigned)li);
+  float2* const rowb = phs + N + li0 * CF::line_stride(FF ? NS : 0);  // staged symbol row of this line
   const long long base = (long long)q * a.rhs_stride + cc * a.comp_stride + (long long)line * N + t;
   const float2* __restrict__ tw = (const float2*)a.fft.tw;
   const float2* __restrict__ ph = (const float2*)a.fft.ph;
@@ -114,7 +122,7 @@ __global__ void __launch_bounds__(LeafCfg<P, C>::THREADS, LeafCfg<P, C>::MINB) k
   auto row_pos = [&](int k) { return k * JP + ((C == 3 && nsym == 6 && (k == 3 || k == 5)) ? 8 : 0); };
   auto stage_row = [&](int bb) {
     if constexpr (FF) {
-      if (!ok) return;
+      if (!ok || li0 != li) return;    // staged by the first line of the block with this spatial line
       const int cl = (clsp << 1) | bb;
       const int J = S.J[cl][dl];
       const float2* src = Sd + S.cls_off[cl] + (long long)lin * J;
@@ -324,7 +332,21 @@ static cudaError_t leaf_reg_c(const LeafArgs& a, cudaStream_t st) {
   return cudaErrorNotSupported;
 }
 
+// The c = 3 split leaf on the compressed block-symmetric store takes the
+// component-in-thread kernel (fast_leaf3.cu) for 64- and 128-point lines,
+// where it measured faster (128^3: 115 against 124 us per launch), and the
+// component-group kernel above for longer lines (256^3: 891 against 901 us).
+// BTMV_LEAF3=0 / 1 in the environment forces one or the other (comparisons).
+static bool use_leaf3(const LeafArgs& a) {
+  if (a.c != 3 || !leaf3_supported(a, sizeof(float2))) return false;
+  const char* v = getenv("BTMV_LEAF3");
+  if (v && v[0] == '0') return false;
+  if (v && v[0] == '1') return true;
+  return a.N <= 128;
+}
+
 cudaError_t launch_leaf_reg(const LeafArgs& a, cudaStream_t st) {
+  if (use_leaf3(a)) return launch_leaf3(a, st);
   return a.c == 1 ? leaf_reg_c<1>(a, st) : leaf_reg_c<3>(a, st);
 }
 

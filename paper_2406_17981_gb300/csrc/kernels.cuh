@@ -172,6 +172,10 @@ bool pass_reg_supported(const PassArgs& a, size_t esz);
 cudaError_t launch_pass_reg(int mode, const PassArgs& a, cudaStream_t st);
 bool leaf_reg_supported(const LeafArgs& a, size_t esz);
 cudaError_t launch_leaf_reg(const LeafArgs& a, cudaStream_t st);
+// c = 3 split leaf with all components of a line in one thread group
+// (fast_leaf3.cu); launch_leaf_reg takes it where supported and faster.
+bool leaf3_supported(const LeafArgs& a, size_t esz);
+cudaError_t launch_leaf3(const LeafArgs& a, cudaStream_t st);
 
 size_t pass_smem_bytes(const PassGeom& g, size_t esz);
 size_t leaf_smem_bytes(int N, int c, int rq, int Lt, size_t esz);

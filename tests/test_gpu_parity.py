@@ -265,6 +265,33 @@ def test_cufft_embedding_vs_oracle(n, c, kind):
         assert rel(y, ref) <= TOL[precision]
 
 
+LEAF3_CASES = [((6, 5, 64), "green", 1), ((5, 3, 64), "green", 3), ((3, 4, 128), "green", 2),
+               ((2, 3, 256), "green", 1), ((2, 2, 512), "green", 2), ((1, 2, 1024), "green", 1),
+               ((4, 6, 128), "skew", 2), ((6, 64), "skew", 3), ((3, 2, 2, 256), "skew", 1)]
+
+
+@pytest.mark.parametrize("n,kind,nrhs", LEAF3_CASES)
+def test_component_in_thread_leaf(n, kind, nrhs, monkeypatch):
+    """The c = 3 leaf that holds all three components of a line in one
+    thread group (64..1024-point lines, compressed block-symmetric store,
+    right-hand sides ordered fastest) against the FP64 oracle and against the
+    component-group leaf (BTMV_LEAF3=0)."""
+    if kind == "skew":
+        t_orth, par = W.skew_orthant(n, seed=91, c=3)
+    else:
+        t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    flags = bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY
+    x = W.random_vector(n, 3, seed=92, nrhs=nrhs)
+    ref = OE.embed_matvec(W.orthant_to_full(t_orth, par), round_input(x, 0))
+    monkeypatch.setenv("BTMV_LEAF3", "0")
+    yg = run_btmv(t_orth, x, n, 3, 0, 0, flags, par)
+    assert rel(yg, ref) <= 1e-5
+    monkeypatch.setenv("BTMV_LEAF3", "1")
+    y3 = run_btmv(t_orth, x, n, 3, 0, 0, flags, par)
+    assert rel(y3, ref) <= 1e-5
+    assert rel(y3, yg) <= 2e-6
+
+
 def test_plan_clone_shares_the_symbol():
     n, c = (10, 12, 8), 3
     t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
