@@ -8,17 +8,18 @@ times beside the operation-count ratio R_c of Eq. CompRatio.  This module does
 the same on the host cores with scipy.fft (``workers`` = the cores this
 process may use), scalar blocks (c = 1):
 
-* ``embed_apply``: pad x to the 2n grid, forward transform, multiply by the
+* ``EmbedRunner``: pad x to the 2n grid, forward transform, multiply by the
   transformed embedded generator, inverse transform, keep the n grid (Sec. I).
-* ``split_apply``: Algorithm 1 (Sec. II.B) depth first over the levels: at
+* ``SplitRunner``: Algorithm 1 (Sec. II.B) depth first over the levels: at
   level m a node is transformed along dim m into its even child DFT_n(v) and
   its odd child DFT_n(P_m v) (Sec. II.A splitting property), the leaf with
   parity vector b multiplies by S_b = S[2l + b], and on the way back the
   children are inverse transformed and merged as R_e + conj(P_m) R_o
   (merging property), which is the eager projection onto the n grid.
 
-The symbol (the transform of the embedded generator) is prepared once per
-problem, outside the timed region, as the paper's timings cover the matvec.
+The symbol (the transform of the embedded generator) and the work arrays are
+prepared once per problem, outside the timed region, as the paper's timings
+cover the matvec; transforms and products then run in place.
 Transforms are unnormalised in both directions; the single 1/prod(2 n_m)
 scale sits in the symbol.  This is a CPU study only: the GPU library does
 not use it.
@@ -34,6 +35,49 @@ import scipy.fft as sfft
 
 def cores() -> int:
     return len(os.sched_getaffinity(0))
+
+
+class Par:
+    """Elementwise products, sums, fills and copies on every core: the arrays
+    are cut along their leading axis into one chunk per worker (numpy ufuncs
+    release the interpreter lock on large arrays), so that these memory-bound
+    passes are as parallel as the library FFTs beside them."""
+
+    def __init__(self, workers: int):
+        import concurrent.futures as cf
+        self.w = max(1, workers)
+        self.pool = cf.ThreadPoolExecutor(max_workers=self.w) if self.w > 1 else None
+
+    def _chunks(self, n0):
+        k = min(self.w, n0)
+        b = [n0 * i // k for i in range(k + 1)]
+        return [slice(b[i], b[i + 1]) for i in range(k)]
+
+    @staticmethod
+    def _part(a, sl):
+        return a if (a.ndim == 0 or a.shape[0] == 1) else a[sl]
+
+    def run(self, fn, out, *args):
+        if self.pool is None or out.shape[0] < 2 or out.size < (1 << 16):
+            fn(*args, out=out)
+            return out
+        futs = [self.pool.submit(fn, *[self._part(a, sl) for a in args], out=out[sl])
+                for sl in self._chunks(out.shape[0])]
+        for f in futs:
+            f.result()
+        return out
+
+    def mul(self, a, b, out):
+        return self.run(np.multiply, out, a, b)
+
+    def add(self, a, b, out):
+        return self.run(np.add, out, a, b)
+
+    def copy(self, src, out):
+        return self.run(lambda a, out: np.copyto(out, a), out, src)
+
+    def zero(self, out):
+        return self.run(lambda out: out.fill(0.0), out)
 
 
 def embedded_symbol(t: np.ndarray, workers: int) -> np.ndarray:
@@ -76,29 +120,72 @@ def phases(n) -> list:
     return out
 
 
+class EmbedRunner:
+    """The full embedding with its 2n-grid work array allocated once and
+    every transform and product done in place (as with in-place library FFT
+    plans)."""
+
+    def __init__(self, S: np.ndarray, workers: int):
+        self.S, self.workers = S, workers
+        self.par = Par(workers)
+        self.Z = np.empty(S.shape, dtype=np.complex128)
+        self.y = None
+
+    def __call__(self, x: np.ndarray) -> np.ndarray:
+        n = x.shape
+        grid = tuple(slice(0, m) for m in n)
+        Z = self.Z
+        self.par.zero(Z)
+        self.par.copy(x, Z[grid])
+        Z = sfft.fftn(Z, workers=self.workers, overwrite_x=True)
+        self.par.mul(Z, self.S, Z)
+        Z = sfft.ifftn(Z, workers=self.workers, norm="forward", overwrite_x=True)
+        if self.y is None:
+            self.y = np.empty(n, dtype=np.complex128)
+        return self.par.copy(Z[grid], self.y)
+
+
+class SplitRunner:
+    """Algorithm 1 depth first with one work array per level (the node
+    vector is transformed in place into its even child, the odd child lives in
+    the level's array): the (d + 1)-vector footprint of Sec. II.C, transforms
+    and products in place."""
+
+    def __init__(self, parts: dict, P: list, workers: int):
+        self.parts, self.P, self.workers = parts, P, workers
+        self.par = Par(workers)
+        self.Pc = [np.conj(p) for p in P]
+        shape = next(iter(parts.values())).shape
+        self.d = len(shape)
+        self.top = np.empty(shape, dtype=np.complex128)
+        self.odd = [np.empty(shape, dtype=np.complex128) for _ in range(self.d)]
+
+    def _node(self, v, m, prefix):
+        if m == self.d:
+            return self.par.mul(v, self.parts[prefix], v)
+        w = self.workers
+        odd = self.odd[m]
+        self.par.mul(v, self.P[m], odd)
+        v = sfft.fft(v, axis=m, workers=w, overwrite_x=True)
+        odd = sfft.fft(odd, axis=m, workers=w, overwrite_x=True)
+        v = self._node(v, m + 1, prefix + (0,))
+        odd = self._node(odd, m + 1, prefix + (1,))
+        v = sfft.ifft(v, axis=m, workers=w, norm="forward", overwrite_x=True)
+        odd = sfft.ifft(odd, axis=m, workers=w, norm="forward", overwrite_x=True)
+        self.par.mul(odd, self.Pc[m], odd)
+        return self.par.add(v, odd, v)
+
+    def __call__(self, x: np.ndarray) -> np.ndarray:
+        self.par.copy(x, self.top)
+        return self._node(self.top, 0, ()).copy()
+
+
 def embed_apply(S: np.ndarray, x: np.ndarray, workers: int) -> np.ndarray:
-    n = x.shape
-    xp = np.zeros(S.shape, dtype=np.complex128)
-    xp[tuple(slice(0, m) for m in n)] = x
-    Y = sfft.fftn(xp, workers=workers)
-    Y *= S
-    y = sfft.ifftn(Y, workers=workers, norm="forward")
-    return y[tuple(slice(0, m) for m in n)]
+    return EmbedRunner(S, workers)(x)
 
 
 def split_apply(parts: dict, P: list, x: np.ndarray, workers: int) -> np.ndarray:
-    d = x.ndim
-
-    def node(v, m, prefix):
-        if m == d:
-            return v * parts[prefix]
-        even = sfft.fft(v, axis=m, workers=workers)
-        odd = sfft.fft(v * P[m], axis=m, workers=workers)
-        re = sfft.ifft(node(even, m + 1, prefix + (0,)), axis=m, workers=workers, norm="forward")
-        ro = sfft.ifft(node(odd, m + 1, prefix + (1,)), axis=m, workers=workers, norm="forward")
-        return re + np.conj(P[m]) * ro
-
-    return node(x, 0, ())
+    return SplitRunner(parts, P, workers)(x)
 
 
 def time_best(fn, repeats: int) -> float:
@@ -131,8 +218,12 @@ def study(sizes=None, repeats: int = 3, seed: int = 11, workers: int | None = No
             S = embedded_symbol(t, workers)
             parts = leaf_parts(S)
             P = phases(n)
-            ts = time_best(lambda: split_apply(parts, P, x, workers), repeats)
-            te = time_best(lambda: embed_apply(S, x, workers), repeats)
+            sr = SplitRunner(parts, P, workers)
+            ts = time_best(lambda: sr(x), repeats)
+            del sr
+            er = EmbedRunner(S, workers)
+            te = time_best(lambda: er(x), repeats)
+            del er
             rows.append({"d": d, "n": nm, "split_s": ts, "embed_s": te, "ratio_embed_over_split": te / ts})
             del S, parts, t
     return rows

@@ -1,7 +1,5 @@
 // Register-resident strided line passes (forward split and merge) for the
 // line lengths fast.cuh provides plans for.
-#include <cstdlib>
-
 #include "fast.cuh"
 
 namespace btmv {
@@ -10,11 +8,6 @@ namespace btmv {
 // columns per tile: 16 x 8 B = 128 B rows; fewer for long lines so that the
 // tile stays within the 48 KB of static shared memory
 template <class P> __host__ __device__ constexpr int pass_cols() { return P::N <= 256 ? 16 : P::N <= 768 ? 8 : 4; }
-// narrow tiles: half the columns (twice the tiles, finer waves); selected
-// with BTMV_PASS_NARROW=1 for comparisons
-template <class P, bool NARROW> __host__ __device__ constexpr int pass_cols_v() {
-  return NARROW && pass_cols<P>() > 4 ? pass_cols<P>() / 2 : pass_cols<P>();
-}
 
 // minimum resident blocks per SM for the radix-16 plans of 128..512 points,
 // scaled to 128-thread blocks: 6 for the forward split (80 registers), 4 for
@@ -24,16 +17,14 @@ template <class P, bool NARROW> __host__ __device__ constexpr int pass_cols_v() 
 // and run unbounded, except the forward split of 160 and 192 points, which
 // fits 4 blocks in 128 registers without spills (2.4% faster at 160^3 and
 // 192^3).
-template <class P, int MODE, bool NARROW = false> __host__ __device__ constexpr int pass_minb() {
-  constexpr int PWv = pass_cols_v<P, NARROW>();
-  constexpr int b = (MODE == 0 ? 6 : 4) * 128 / (PWv * P::T);
-  if (MODE == 0 && (P::N == 160 || P::N == 192)) return 4 * 128 / (PWv * P::T);  // 128 registers
+template <class P, int MODE> __host__ __device__ constexpr int pass_minb() {
+  constexpr int b = (MODE == 0 ? 6 : 4) * 128 / (pass_cols<P>() * P::T);
+  if (MODE == 0 && (P::N == 160 || P::N == 192)) return 4 * 128 / (pass_cols<P>() * P::T);  // 128 registers
   return (P::R1 == 16 && P::N >= 128 && P::N <= 512 && b > 0) ? b : 1;
 }
-template <class P, int MODE, bool NARROW>
-__global__ void __launch_bounds__(pass_cols_v<P, NARROW>() * P::T, pass_minb<P, MODE, NARROW>())
-    k_pass_reg(const PassArgs a) {
-  constexpr int R1 = P::R1, TT = P::T, N = P::N, PW = pass_cols_v<P, NARROW>();
+template <class P, int MODE>
+__global__ void __launch_bounds__(pass_cols<P>() * P::T, pass_minb<P, MODE>()) k_pass_reg(const PassArgs a) {
+  constexpr int R1 = P::R1, TT = P::T, N = P::N, PW = pass_cols<P>();
   __shared__ float2 sm[N * PW];
   const int col = threadIdx.x % PW;
   const int t = threadIdx.x / PW;
@@ -98,29 +89,19 @@ __global__ void __launch_bounds__(pass_cols_v<P, NARROW>() * P::T, pass_minb<P, 
   }
 }
 
-template <class P, bool NARROW>
-static cudaError_t pass_reg_pn(int mode, const PassArgs& a, cudaStream_t st) {
-  constexpr int PW = pass_cols_v<P, NARROW>();
+template <class P>
+static cudaError_t pass_reg_p(int mode, const PassArgs& a, cudaStream_t st) {
+  constexpr int PW = pass_cols<P>();
   const long long nt = (a.g.lines + PW - 1) / PW;
   if (nt <= 0) return cudaSuccess;
 #ifndef BTMV_NO_PDL
-  if (mode == 0) return launch_pdl(k_pass_reg<P, 0, NARROW>, dim3((unsigned)nt), dim3(PW * P::T), 0, st, a);
-  return launch_pdl(k_pass_reg<P, 1, NARROW>, dim3((unsigned)nt), dim3(PW * P::T), 0, st, a);
+  if (mode == 0) return launch_pdl(k_pass_reg<P, 0>, dim3((unsigned)nt), dim3(PW * P::T), 0, st, a);
+  return launch_pdl(k_pass_reg<P, 1>, dim3((unsigned)nt), dim3(PW * P::T), 0, st, a);
 #else
-  if (mode == 0) k_pass_reg<P, 0, NARROW><<<(unsigned)nt, PW * P::T, 0, st>>>(a);
-  else           k_pass_reg<P, 1, NARROW><<<(unsigned)nt, PW * P::T, 0, st>>>(a);
+  if (mode == 0) k_pass_reg<P, 0><<<(unsigned)nt, PW * P::T, 0, st>>>(a);
+  else           k_pass_reg<P, 1><<<(unsigned)nt, PW * P::T, 0, st>>>(a);
   return cudaGetLastError();
 #endif
-}
-
-static bool pass_narrow() {
-  const char* v = getenv("BTMV_PASS_NARROW");
-  return v && v[0] == '1';
-}
-
-template <class P>
-static cudaError_t pass_reg_p(int mode, const PassArgs& a, cudaStream_t st) {
-  return pass_narrow() ? pass_reg_pn<P, true>(mode, a, st) : pass_reg_pn<P, false>(mode, a, st);
 }
 
 bool pass_reg_supported(const PassArgs& a, size_t esz) {
