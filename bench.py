@@ -85,7 +85,7 @@ def measured_peaks():
 # source files that define each kernel kind bench.py reports on; a recorded
 # ncu figure is used only while these files are unchanged
 KERNEL_SOURCES = {
-    "leaf": ["fast_leaf.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
+    "leaf": ["fast_leaf.cu", "fast_leaf3.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
     "fwd_split": ["fast_pass.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
     "merge": ["fast_pass.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
 }

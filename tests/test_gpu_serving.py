@@ -55,7 +55,10 @@ def test_solves_alone_and_in_the_mix_agree():
             spec.max_matvecs, spec.tol, 0.0, spec.name)])
         a = alone["solutions"][spec.name].cpu().numpy().astype(np.complex128)
         m = mix["solutions"][spec.name].cpu().numpy().astype(np.complex128)
-        assert rel(m, a) <= 1e-4, spec.name
+        assert rel(m, a) <= 1e-5, spec.name
+        # each request of a tick runs the problem's own kernels on a forked
+        # stream, so a solve in the mix repeats its alone run bit for bit
+        assert np.array_equal(m, a), spec.name
     # every recorded matvec of the mix equals the same matvec done alone
     for name, pairs in record.items():
         spec = specs[int(name[1:])]
@@ -66,6 +69,7 @@ def test_solves_alone_and_in_the_mix_agree():
             p.apply(x, ya, 1)
             torch.cuda.synchronize()
             assert rel(y.cpu().numpy().astype(np.complex128), ya.cpu().numpy().astype(np.complex128)) <= 1e-5
+            assert torch.equal(y, ya)
         p.close()
 
 
@@ -106,7 +110,7 @@ def test_client_that_aborts_mid_solve():
     for spec in (specs[0], specs[2], specs[3]):
         a = _alone(spec)["solutions"][spec.name].cpu().numpy().astype(np.complex128)
         m = out["solutions"][spec.name].cpu().numpy().astype(np.complex128)
-        assert rel(m, a) <= 1e-4, spec.name
+        assert rel(m, a) <= 1e-5, spec.name
     # only the resident operators' symbols are still counted against the budget
     assert out["budget_in_use_at_end"] == sum(s.symbol_footprint() for s in specs)
 
@@ -144,7 +148,7 @@ def test_failed_batch_is_retried_one_solve_at_a_time(monkeypatch):
     for spec in specs:
         a = _alone(spec)["solutions"][spec.name].cpu().numpy().astype(np.complex128)
         m = out["solutions"][spec.name].cpu().numpy().astype(np.complex128)
-        assert rel(m, a) <= 1e-4, spec.name
+        assert rel(m, a) <= 1e-5, spec.name
 
 
 def test_solve_whose_apply_fails_is_reported(monkeypatch):
@@ -181,4 +185,4 @@ def test_solve_whose_apply_fails_is_reported(monkeypatch):
     for spec in (specs[0], specs[1], specs[3]):
         a = _alone(spec)["solutions"][spec.name].cpu().numpy().astype(np.complex128)
         m = out["solutions"][spec.name].cpu().numpy().astype(np.complex128)
-        assert rel(m, a) <= 1e-4, spec.name
+        assert rel(m, a) <= 1e-5, spec.name
