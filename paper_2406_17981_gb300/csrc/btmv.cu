@@ -112,8 +112,10 @@ static btmv_status build_tables(btmv_plan p, const std::vector<int>& Nf, const s
   return BTMV_OK;
 }
 
+// complex128 transforms take radix-8-first plans: a radix-16 butterfly on
+// double2 holds 32 registers of values plus as many temporaries per thread
 static void set_fft(btmv_plan p, FftDev& f, int N, bool dbl) {
-  factor_radices(N, f);
+  factor_radices_mode(N, f, dbl ? 1 : 0);
   const size_t off = dbl ? p->tab.off_d[N] : p->tab.off_f[N];
   const size_t esz = dbl ? sizeof(double2) : sizeof(float2);
   f.tw = (const unsigned char*)p->tab.mem + off;
