@@ -86,8 +86,15 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, unsigned char* smem
   int* okl = (int*)(offs + 4 * TL);           // [TL]
   T* B0 = (T*)(smem + pass_hdr_bytes(TL));
   T* B1 = B0 + bufsz;
-  T* B2 = B1 + bufsz;
+  T* B2 = B1 + bufsz;                         // B2, B3: scratch of a two-half transform
   const T* ph = (const T*)a.fft.ph;
+  // two halves (both children of a split, both inputs of a merge) are
+  // transformed together as one tile of 2 TL lines in B0..B1: the second
+  // half's lines follow the first's (line-major tiles) or interleave with
+  // element stride 2 TL (line-fast tiles), so each Stockham stage serves
+  // both halves and the number of dependent stages per tile is halved
+  const int es2 = g.contig ? 1 : 2 * TL;
+  const int h2 = g.contig ? TL * ls : TL;     // offset of the second half's line 0
 
   const long long tile0 = tile * TL;
   for (int l = threadIdx.x; l < TL; l += blockDim.x) {
@@ -116,13 +123,11 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, unsigned char* smem
   if (MODE == 0) {
     const bool both = a.out0 && a.out1;
     if (both) {
-      pass_load<T>(B0, B1, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es, ph, false);
+      pass_load<T>(B0, B0 + h2, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es2, ph, false);
       __syncthreads();
-      T* r0 = fft_lines<false, LF>(B0, B2, TL, ls, es, a.fft);
-      pass_store<T>((T*)a.out0, r0, nullptr, a.a_out0, offs + 2 * TL, okl, g, ls, es, ph);
-      __syncthreads();
-      T* r1 = fft_lines<false, LF>(B1, (r0 == B0) ? B2 : B0, TL, ls, es, a.fft);
-      pass_store<T>((T*)a.out1, r1, nullptr, a.a_out1, offs + 3 * TL, okl, g, ls, es, ph);
+      T* r = fft_lines<false, LF>(B0, B2, 2 * TL, ls, es2, a.fft);
+      pass_store<T>((T*)a.out0, r, nullptr, a.a_out0, offs + 2 * TL, okl, g, ls, es2, ph);
+      pass_store<T>((T*)a.out1, r + h2, nullptr, a.a_out1, offs + 3 * TL, okl, g, ls, es2, ph);
     } else {
       const bool odd = a.out1 != nullptr;
       pass_load<T>(B0, nullptr, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es, ph, odd);
@@ -133,13 +138,18 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, unsigned char* smem
     }
   } else {
     const bool two = a.in1 != nullptr;
-    pass_load<T>(B0, nullptr, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es, ph, false);
-    if (two) pass_load<T>(B1, nullptr, (const T*)a.in1, a.a_in1, offs + TL, okl, g, ls, es, ph, false);
-    __syncthreads();
-    T* r0 = fft_lines<true, LF>(B0, B2, TL, ls, es, a.fft);
-    T* r1 = nullptr;
-    if (two) r1 = fft_lines<true, LF>(B1, (r0 == B0) ? B2 : B0, TL, ls, es, a.fft);
-    pass_store<T>((T*)a.out0, r0, r1, a.a_out0, offs + 2 * TL, okl, g, ls, es, ph);
+    if (two) {
+      pass_load<T>(B0, nullptr, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es2, ph, false);
+      pass_load<T>(B0 + h2, nullptr, (const T*)a.in1, a.a_in1, offs + TL, okl, g, ls, es2, ph, false);
+      __syncthreads();
+      T* r = fft_lines<true, LF>(B0, B2, 2 * TL, ls, es2, a.fft);
+      pass_store<T>((T*)a.out0, r, r + h2, a.a_out0, offs + 2 * TL, okl, g, ls, es2, ph);
+    } else {
+      pass_load<T>(B0, nullptr, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es, ph, false);
+      __syncthreads();
+      T* r0 = fft_lines<true, LF>(B0, B2, TL, ls, es, a.fft);
+      pass_store<T>((T*)a.out0, r0, nullptr, a.a_out0, offs + 2 * TL, okl, g, ls, es, ph);
+    }
   }
 }
 
@@ -327,6 +337,9 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, unsigned char* smem
   const int ls = N | 1;
   const int bufsz = NV * ls;
   int* fpre = (int*)smem;                    // [Lt][FPS]: f of line dims, valid flag
+  // X | B0: the odd half's lines (twiddled input), then the even half's; the
+  // split leaf transforms both halves as one tile of 2 NV lines (each
+  // Stockham stage serves both), with B1..B2 as scratch
   T* X = (T*)(smem + leaf_hdr_bytes(Lt));
   T* B0 = X + bufsz;
   T* B1 = B0 + bufsz;
@@ -370,19 +383,21 @@ __device__ __forceinline__ void leaf_body(const LeafArgs& a, unsigned char* smem
   }
   __syncthreads();
 
-  // even half (or the whole 2n line for the plain embedding)
-  T* r = fft_lines<false, false>(B0, B1, NV, ls, 1, a.fft);
-  leaf_multiply_any<T>(r, a, 0, fpre, ls);
-  __syncthreads();
-  T* A0 = fft_lines<true, false>(r, (r == B0) ? B1 : B0, NV, ls, 1, a.fft);
+  T* A0;
   T* A1 = nullptr;
   if (a.split) {
-    // odd half: twiddled input in X, scratch = the buffer not holding A0
-    T* S = (A0 == B0) ? B1 : B0;
-    T* r1 = fft_lines<false, false>(X, S, NV, ls, 1, a.fft);
-    leaf_multiply_any<T>(r1, a, 1, fpre, ls);
+    T* r = fft_lines<false, false>(X, B1, 2 * NV, ls, 1, a.fft);
+    leaf_multiply_any<T>(r + bufsz, a, 0, fpre, ls);   // even half
+    leaf_multiply_any<T>(r, a, 1, fpre, ls);           // odd half
     __syncthreads();
-    A1 = fft_lines<true, false>(r1, (r1 == X) ? S : X, NV, ls, 1, a.fft);
+    A1 = fft_lines<true, false>(r, (r == X) ? B1 : X, 2 * NV, ls, 1, a.fft);
+    A0 = A1 + bufsz;
+  } else {
+    // the whole 2n line (plain embedding)
+    T* r = fft_lines<false, false>(B0, B1, NV, ls, 1, a.fft);
+    leaf_multiply_any<T>(r, a, 0, fpre, ls);
+    __syncthreads();
+    A0 = fft_lines<true, false>(r, (r == B0) ? B1 : B0, NV, ls, 1, a.fft);
   }
 
   T* __restrict__ out = (T*)nd.out;

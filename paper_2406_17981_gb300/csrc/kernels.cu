@@ -24,12 +24,12 @@ namespace btmv {
 size_t pass_smem_bytes(const PassGeom& g, size_t esz) {
   const size_t ls = g.contig ? (size_t)(g.N | 1) : 1;
   const size_t buf = g.contig ? (size_t)g.TL * ls : (size_t)g.TL * g.N;
-  return pass_hdr_bytes(g.TL) + 3 * buf * esz;
+  return pass_hdr_bytes(g.TL) + 4 * buf * esz;     // two-half tile + its scratch
 }
 
 size_t leaf_smem_bytes(int N, int c, int rq, int Lt, size_t esz) {
   const size_t ls = (size_t)(N | 1);
-  return leaf_hdr_bytes(Lt) + 3 * (size_t)rq * c * Lt * ls * esz;
+  return leaf_hdr_bytes(Lt) + 4 * (size_t)rq * c * Lt * ls * esz;   // two-half tile + its scratch
 }
 
 template <class T, int MODE>
