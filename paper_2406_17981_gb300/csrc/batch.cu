@@ -1,17 +1,25 @@
-// btmv_apply_batched: many independent split applies in ONE persistent
-// kernel launch (k_persistent), replayed from a captured CUDA graph.
+// btmv_apply_batched: many independent split applies per call, replayed from
+// a CUDA graph captured once per argument set, in one of two execution modes
+// chosen per problem mix by an autotuner:
 //
-// Each problem contributes the steps of its depth-first schedule (the same
-// steps btmv_apply launches one by one) as a chain of stages, each waiting
-// for the previous one of the same problem.  Stages are ordered step-slot by
-// step-slot across problems, so different problems' passes run side by side
-// on the GPU while each problem keeps the (d+1)-vector peak of its plan.
+//   mode 0  ONE persistent kernel launch (k_persistent).  Each problem
+//           contributes the steps of its depth-first schedule (the same steps
+//           btmv_apply launches one by one) as a chain of stages, each
+//           waiting for the previous one of the same problem.  Stages are
+//           ordered step-slot by step-slot across problems, so different
+//           problems' passes run side by side on the GPU while each problem
+//           keeps the (d+1)-vector peak of its plan.  It runs the generic
+//           shared-memory line bodies.
+//   mode 1  one graph whose parallel branches (16, 4 or 1) run the problems'
+//           own register-kernel launches, largest problems first.
 //
-// The tile sizes and radix order of the line passes are chosen per batch
-// signature (problem shapes, components, right-hand sides) by a small
-// coordinate-descent autotuner that times candidate launches with CUDA
-// events on the caller's data, keeps the winner for the process and, when the
-// environment variable BTMV_TUNE_CACHE names a file, in that file.
+// The autotuner times both: for mode 0 a small coordinate descent over the
+// tile sizes and radix order of the line bodies, for mode 1 each branch
+// count, with CUDA events on the caller's data; it keeps the winner for the
+// process and, when the environment variable BTMV_TUNE_CACHE names a file, in
+// that file.  On mixes of large problems mode 1 wins (the register kernels
+// are specialised per line length); BTMV_NO_AUTOTUNE with BTMV_BATCH_MODE=0|1
+// fixes the mode.
 #include <cuda_runtime.h>
 
 #include <algorithm>
