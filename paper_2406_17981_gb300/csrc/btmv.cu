@@ -125,6 +125,7 @@ static void set_fft(btmv_plan p, FftDev& f, int N, bool dbl) {
 static void free_plan(btmv_plan p) {
   if (!p) return;
   cufft_plan_destroy(p);
+  if (p->tma_err_host) cudaFreeHost(p->tma_err_host);
   for (auto& r : p->pending) { p->pool.push_back(r.a); p->pool.push_back(r.b); }
   for (auto e : p->pool) cudaEventDestroy(e);
   p->tab.owner.reset();       // freed with the last plan sharing them
@@ -182,6 +183,16 @@ static btmv_status setup_padding(btmv_plan p, size_t V) {
   if (cudaMalloc(&p->xpad, V) != cudaSuccess || cudaMalloc(&p->ypad, V) != cudaSuccess)
     return fail(BTMV_E_NOMEM, "plan: padded x and y of %zu bytes", V);
   p->ws_bytes += 2 * V;
+  return BTMV_OK;
+}
+
+// The host-mapped error word of the TMA-staged passes.
+static btmv_status setup_tma_error_word(btmv_plan p) {
+  if (cudaHostAlloc((void**)&p->tma_err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
+    return fail(BTMV_E_NOMEM, "plan: host-mapped error word");
+  *p->tma_err_host = 0;
+  if (cudaHostGetDevicePointer((void**)&p->tma_err_dev, p->tma_err_host, 0) != cudaSuccess)
+    return fail(BTMV_E_CUDA, "plan: device address of the host-mapped error word");
   return BTMV_OK;
 }
 
@@ -271,6 +282,8 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
     st = cufft_plan_setup(p);
     if (st != BTMV_OK) { free_plan(p); return st; }
   }
+  st = setup_tma_error_word(p);
+  if (st != BTMV_OK) { free_plan(p); return st; }
   read_profile_every(p);
   *out = p;
   return BTMV_OK;
@@ -312,6 +325,8 @@ extern "C" btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flag
       st = cufft_plan_setup(p);
       if (st != BTMV_OK) { free_plan(p); return st; }
     }
+    st = setup_tma_error_word(p);
+    if (st != BTMV_OK) { free_plan(p); return st; }
   }
   read_profile_every(p);
   *out = p;
@@ -632,9 +647,26 @@ static void choose_tile(PassGeom& g, size_t esz) {
 
 // Register-resident kernels where the geometry allows, else the generic
 // shared-memory kernels (or always the generic ones with BTMV_FLAG_GENERIC).
+// The TMA-staged passes (fast_pass_tma.cu) take the merge of 256-point lines
+// and the forward split of 128-point lines, where they measured faster than
+// the register passes (256^3 merge 201 against 216 us, 128^3 forward split
+// 28.7 against 29.8 us; slower in the other two cases).  BTMV_PASS_TMA=0 / 1
+// in the environment turns them off / on for every pass they can take
+// (comparisons).
+static bool use_pass_tma(int mode, const PassArgs& pa) {
+  const char* v = getenv("BTMV_PASS_TMA");
+  if (v && v[0] == '0') return false;
+  if (v && v[0] == '1') return true;
+  return (mode == 1 && pa.g.N == 256) || (mode == 0 && pa.g.N == 128);
+}
+
 template <class T>
 static cudaError_t run_pass(btmv_plan p, int mode, const PassArgs& pa, cudaStream_t st) {
-  if (!(p->flags & BTMV_FLAG_GENERIC) && pass_reg_supported(pa, sizeof(T))) return launch_pass_reg(mode, pa, st);
+  if (!(p->flags & BTMV_FLAG_GENERIC) && pass_reg_supported(pa, sizeof(T))) {
+    if (p->tma_err_dev && use_pass_tma(mode, pa) && pass_tma_supported(mode, pa, sizeof(T)))
+      return launch_pass_tma(mode, pa, p->tma_err_dev, st);
+    return launch_pass_reg(mode, pa, st);
+  }
   return launch_pass<T>(mode, pa, st);
 }
 
@@ -662,6 +694,10 @@ PassArgs btmv::split_pass_args(btmv_plan p, const Step& stp, int nrhs, size_t es
 template <class T>
 static btmv_status split_pass(btmv_plan p, const Step& stp, int nrhs, cudaStream_t st) {
   const int mode = stp.kind;
+  if (p->tma_err_host && *(volatile int*)p->tma_err_host) {
+    *(volatile int*)p->tma_err_host = 0;
+    return fail(BTMV_E_TIMEOUT, "split pass: a bounded wait for a TMA tile expired in an earlier launch");
+  }
   PassArgs pa = split_pass_args(p, stp, nrhs, sizeof(T), 0);
   ProfScope ps(p, mode == 0 ? BTMV_K_FWD_SPLIT : BTMV_K_MERGE, st);
   cudaError_t e = run_pass<T>(p, mode, pa, st);

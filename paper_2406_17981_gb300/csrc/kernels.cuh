@@ -170,6 +170,11 @@ cudaError_t launch_store(const StoreArgs& a, cudaStream_t st);
 // *_supported checks say whether a launch can take them.
 bool pass_reg_supported(const PassArgs& a, size_t esz);
 cudaError_t launch_pass_reg(int mode, const PassArgs& a, cudaStream_t st);
+// the same passes with TMA-staged input tiles and persistent blocks
+// (fast_pass_tma.cu); err: device address of a word set to 1 when a bounded
+// wait expired
+bool pass_tma_supported(int mode, const PassArgs& a, size_t esz);
+cudaError_t launch_pass_tma(int mode, const PassArgs& a, int* err, cudaStream_t st);
 bool leaf_reg_supported(const LeafArgs& a, size_t esz);
 cudaError_t launch_leaf_reg(const LeafArgs& a, cudaStream_t st);
 // c = 3 split leaf with all components of a line in one thread group

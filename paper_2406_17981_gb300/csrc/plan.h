@@ -71,6 +71,10 @@ struct btmv_plan_s {
   // BTMV_ALGO_FULL_CUFFT: the cuFFT plan (cufftHandle) of one right-hand side
   int cufft = 0;
   bool has_cufft = false;
+  // TMA-staged passes: host-mapped word the kernels set when a bounded wait
+  // expired (read and cleared by the next pass launch on the host)
+  int* tma_err_host = nullptr;
+  int* tma_err_dev = nullptr;
   // host staging
   void* stage_x = nullptr;
   void* stage_y = nullptr;

@@ -292,6 +292,27 @@ def test_component_in_thread_leaf(n, kind, nrhs, monkeypatch):
     assert rel(y3, yg) <= 2e-6
 
 
+TMA_SIZES = [(32, 64), (64, 32, 128), (16, 32, 64), (128, 128, 16), (256, 32), (32, 256, 16), (64, 64, 64)]
+
+
+@pytest.mark.parametrize("n", TMA_SIZES)
+@pytest.mark.parametrize("c", [1, 3])
+def test_tma_staged_passes(n, c, monkeypatch):
+    """The strided passes with TMA-staged input tiles (persistent blocks,
+    2-D box copies completing on mbarriers) do the same arithmetic as the
+    register passes: the apply must match the FP64 oracle and the default
+    kernels bit for bit."""
+    t = W.random_generator(n, c, seed=400 + sum(n))
+    x = W.random_vector(n, c, seed=401, nrhs=2)
+    monkeypatch.setenv("BTMV_PASS_TMA", "0")
+    y0 = run_btmv(t, x, n, c, 0, 0)
+    monkeypatch.setenv("BTMV_PASS_TMA", "1")
+    y1 = run_btmv(t, x, n, c, 0, 0)
+    ref = OE.embed_matvec(t, round_input(x, 0))
+    assert rel(y1, ref) <= 1e-5
+    assert np.array_equal(y0, y1)
+
+
 def test_plan_clone_shares_the_symbol():
     n, c = (10, 12, 8), 3
     t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
