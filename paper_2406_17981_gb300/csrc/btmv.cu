@@ -647,17 +647,18 @@ static void choose_tile(PassGeom& g, size_t esz) {
 
 // Register-resident kernels where the geometry allows, else the generic
 // shared-memory kernels (or always the generic ones with BTMV_FLAG_GENERIC).
-// The TMA-staged passes (fast_pass_tma.cu) take the merge of 256-point lines
-// and the forward split of 128-point lines, where they measured faster than
-// the register passes (256^3 merge 201 against 216 us, 128^3 forward split
-// 28.7 against 29.8 us; slower in the other two cases).  BTMV_PASS_TMA=0 / 1
-// in the environment turns them off / on for every pass they can take
-// (comparisons).
+// The TMA-staged passes (fast_pass_tma.cu) take the merge of 256-point lines,
+// where they measured faster than the register passes (256^3: 201 against
+// 216 us).  The 128-point forward split was faster with one right-hand side
+// (28.7 against 29.8 us) but slower with sixteen (128^3 r16: 2822 against
+// 2953 rhs-matvecs/s over the apply), and the other cases slower, so the
+// register passes keep them.  BTMV_PASS_TMA=0 / 1 in the environment turns
+// the TMA passes off / on for every pass they can take (comparisons).
 static bool use_pass_tma(int mode, const PassArgs& pa) {
   const char* v = getenv("BTMV_PASS_TMA");
   if (v && v[0] == '0') return false;
   if (v && v[0] == '1') return true;
-  return (mode == 1 && pa.g.N == 256) || (mode == 0 && pa.g.N == 128);
+  return mode == 1 && pa.g.N == 256;
 }
 
 template <class T>

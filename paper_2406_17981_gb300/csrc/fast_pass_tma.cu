@@ -20,8 +20,8 @@
 // host), drains its other copies in flight (again bounded) and returns.
 #include <cuda.h>
 
+#include <algorithm>
 #include <atomic>
-#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
