@@ -135,8 +135,10 @@ enum {
  * Allocates the twiddle tables and the workspace: (d - 1) vectors of
  * max_rhs * c * prod(n) complex for SPLIT (the paper's (d+1)-vector peak with
  * x and y, Sec. II.C), 2^d such vectors for FULL and FULL_CUFFT (plus
- * cuFFT's own work area for FULL_CUFFT).  The device is the current
- * CUDA device.  Errors: BTMV_E_ARG, BTMV_E_UNSUPPORTED, BTMV_E_NOMEM, BTMV_E_CUDA.
+ * cuFFT's own work area for FULL_CUFFT), and one word of pinned, device-mapped
+ * host memory in which the TMA-staged passes report an expired wait.  The
+ * device is the current CUDA device.
+ * Errors: BTMV_E_ARG, BTMV_E_UNSUPPORTED, BTMV_E_NOMEM, BTMV_E_CUDA.
  */
 BTMV_API btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n, int c,
                              int precision, int algo, int max_rhs, uint32_t flags);
@@ -190,7 +192,9 @@ BTMV_API btmv_status btmv_set_kernel(btmv_plan p, const double* t, uint32_t sym_
  * SPLIT: depth-first traversal of Algorithm 1 -- forward split passes along
  * levels 1..d-1, a fused leaf pass along level d (both halves, symbol
  * multiply, merge), merge passes back up; peak (d+1) vectors.
- * Errors: BTMV_E_ARG, BTMV_E_STATE (no generator set), BTMV_E_CUDA.
+ * Errors: BTMV_E_ARG, BTMV_E_STATE (no generator set), BTMV_E_CUDA,
+ * BTMV_E_TIMEOUT (a bounded wait of a TMA-staged pass expired in an earlier
+ * apply on this plan; reported once, by the next apply).
  */
 BTMV_API btmv_status btmv_apply(btmv_plan p, const void* x, void* y, int nrhs, void* stream);
 
