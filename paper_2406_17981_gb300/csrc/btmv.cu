@@ -681,6 +681,7 @@ PassArgs btmv::split_pass_args(btmv_plan p, const Step& stp, int nrhs, size_t es
   const int N = p->n[m];
   pa.g.N = N; pa.g.ni = inner > 1 ? 1 : 0; pa.g.I[0] = (int)inner; pa.g.Itot = inner;
   pa.g.lines = outer * inner; pa.g.contig = inner == 1;
+  pa.g.halves = ((stp.kind == 0 && stp.out0 && stp.out1) || (stp.kind == 1 && stp.in1)) ? 2 : 1;
   choose_tile(pa.g, esz);
   if (TL > 0) {
     pa.g.TL = TL;

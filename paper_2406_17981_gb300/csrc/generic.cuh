@@ -122,12 +122,21 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, unsigned char* smem
 
   if (MODE == 0) {
     const bool both = a.out0 && a.out1;
-    if (both) {
+    if (both && g.halves == 2) {
       pass_load<T>(B0, B0 + h2, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es2, ph, false);
       __syncthreads();
       T* r = fft_lines<false, LF>(B0, B2, 2 * TL, ls, es2, a.fft);
       pass_store<T>((T*)a.out0, r, nullptr, a.a_out0, offs + 2 * TL, okl, g, ls, es2, ph);
       pass_store<T>((T*)a.out1, r + h2, nullptr, a.a_out1, offs + 3 * TL, okl, g, ls, es2, ph);
+    } else if (both) {
+      // both children, one after the other (three tile buffers)
+      pass_load<T>(B0, B1, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es, ph, false);
+      __syncthreads();
+      T* r0 = fft_lines<false, LF>(B0, B2, TL, ls, es, a.fft);
+      pass_store<T>((T*)a.out0, r0, nullptr, a.a_out0, offs + 2 * TL, okl, g, ls, es, ph);
+      __syncthreads();
+      T* r1 = fft_lines<false, LF>(B1, (r0 == B0) ? B2 : B0, TL, ls, es, a.fft);
+      pass_store<T>((T*)a.out1, r1, nullptr, a.a_out1, offs + 3 * TL, okl, g, ls, es, ph);
     } else {
       const bool odd = a.out1 != nullptr;
       pass_load<T>(B0, nullptr, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es, ph, odd);
@@ -138,12 +147,20 @@ __device__ __forceinline__ void pass_body(const PassArgs& a, unsigned char* smem
     }
   } else {
     const bool two = a.in1 != nullptr;
-    if (two) {
+    if (two && g.halves == 2) {
       pass_load<T>(B0, nullptr, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es2, ph, false);
       pass_load<T>(B0 + h2, nullptr, (const T*)a.in1, a.a_in1, offs + TL, okl, g, ls, es2, ph, false);
       __syncthreads();
       T* r = fft_lines<true, LF>(B0, B2, 2 * TL, ls, es2, a.fft);
       pass_store<T>((T*)a.out0, r, r + h2, a.a_out0, offs + 2 * TL, okl, g, ls, es2, ph);
+    } else if (two) {
+      // both inputs, one after the other (three tile buffers)
+      pass_load<T>(B0, nullptr, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es, ph, false);
+      pass_load<T>(B1, nullptr, (const T*)a.in1, a.a_in1, offs + TL, okl, g, ls, es, ph, false);
+      __syncthreads();
+      T* r0 = fft_lines<true, LF>(B0, B2, TL, ls, es, a.fft);
+      T* r1 = fft_lines<true, LF>(B1, (r0 == B0) ? B2 : B0, TL, ls, es, a.fft);
+      pass_store<T>((T*)a.out0, r0, r1, a.a_out0, offs + 2 * TL, okl, g, ls, es, ph);
     } else {
       pass_load<T>(B0, nullptr, (const T*)a.in0, a.a_in0, offs, okl, g, ls, es, ph, false);
       __syncthreads();

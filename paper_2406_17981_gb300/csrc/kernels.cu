@@ -24,7 +24,7 @@ namespace btmv {
 size_t pass_smem_bytes(const PassGeom& g, size_t esz) {
   const size_t ls = g.contig ? (size_t)(g.N | 1) : 1;
   const size_t buf = g.contig ? (size_t)g.TL * ls : (size_t)g.TL * g.N;
-  return pass_hdr_bytes(g.TL) + 4 * buf * esz;     // two-half tile + its scratch
+  return pass_hdr_bytes(g.TL) + (g.halves == 2 ? 4 : 3) * buf * esz;   // (two-half) tile + scratch
 }
 
 size_t leaf_smem_bytes(int N, int c, int rq, int Lt, size_t esz) {

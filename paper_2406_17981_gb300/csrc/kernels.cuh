@@ -29,6 +29,9 @@ struct PassGeom {
   long long lines;   // outer count * Itot
   int TL;            // lines per tile
   int contig;        // 1: element stride 1 (line-major smem), 0: line-fast smem
+  int halves;        // 2: a tile transforms two halves at once (both children
+                     // of a forward split, both inputs of a merge): four tile
+                     // buffers of shared memory instead of three
 };
 
 // Forward split pass (MODE 0): out0 = FFT(in0), out1 = FFT(P in0); either
