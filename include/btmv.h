@@ -308,6 +308,18 @@ BTMV_API btmv_status btmv_batch_tuning(int count, const btmv_plan* plans, const 
  */
 BTMV_API btmv_status btmv_selftest_wait_timeout(int timeout_ms, void* stream);
 
+/*
+ * btmv_selftest_tma_timeout -- failure-detection self test of the bounded
+ * waits of the TMA-staged strided passes: launches one such pass on a small
+ * scratch tile whose mbarrier is told to expect 16 bytes more than the copy
+ * delivers, so that its wait expires after timeout_ms (1..10000).  Returns
+ * BTMV_E_TIMEOUT when the kernel reported the expired wait and returned
+ * normally (the expected outcome; the CUDA context stays usable),
+ * BTMV_E_STATE if no expiry was reported, BTMV_E_CUDA on other failures.
+ * Allocates and frees its scratch; synchronises stream.
+ */
+BTMV_API btmv_status btmv_selftest_tma_timeout(int timeout_ms, void* stream);
+
 /* btmv_destroy -- free every device and host resource of the plan (NULL ok).
  * Synchronises the device work of the plan first. */
 BTMV_API btmv_status btmv_destroy(btmv_plan p);

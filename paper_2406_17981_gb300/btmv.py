@@ -72,8 +72,10 @@ def lib() -> ctypes.CDLL:
         L.btmv_batch_tuning.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.btmv_selftest_wait_timeout.argtypes = [i32, vp]
+        L.btmv_selftest_tma_timeout.argtypes = [i32, vp]
         for name in ("btmv_plan_create", "btmv_plan_clone", "btmv_set_kernel", "btmv_apply", "btmv_apply_host_noalloc",
                      "btmv_apply_batched", "btmv_batch_tuning", "btmv_selftest_wait_timeout",
+                     "btmv_selftest_tma_timeout",
                      "btmv_destroy", "btmv_plan_get_info", "btmv_get_symbol", "btmv_profile_read"):
             getattr(L, name).restype = st
         _lib = L
@@ -181,6 +183,12 @@ def btmv_selftest_wait_timeout(timeout_ms=200, stream=None) -> int:
     """Runs the bounded-wait self test; returns the status code (expected:
     BTMV_E_TIMEOUT)."""
     return lib().btmv_selftest_wait_timeout(int(timeout_ms), _stream(stream))
+
+
+def btmv_selftest_tma_timeout(timeout_ms=50, stream=None) -> int:
+    """Runs the self test of the TMA-staged passes' bounded waits; returns the
+    status code (expected: BTMV_E_TIMEOUT)."""
+    return lib().btmv_selftest_tma_timeout(int(timeout_ms), _stream(stream))
 
 
 def btmv_destroy(plan):

@@ -25,6 +25,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "../../include/btmv.h"
 #include "fast.cuh"
 
 namespace btmv {
@@ -57,10 +58,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // true once the phase with the given parity has completed; false if the
-// wait was abandoned after kWaitLimit rounds
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// wait was abandoned after kWaitLimit rounds or limit_ns nanoseconds
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit_ns) {
   const unsigned a = smem_u32(bar);
+  const unsigned long long t0 = global_ns();
   for (unsigned i = 0; i < kWaitLimit; ++i) {
     unsigned done;
     asm volatile(
@@ -69,6 +77,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((i & 63) == 63 && global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -95,7 +104,7 @@ template <class P, int MODE, int NSTAGE> struct TmaCfg {
 template <class P, int MODE, int NSTAGE>
 __global__ void __launch_bounds__(TmaCfg<P, MODE, NSTAGE>::THREADS)
     k_pass_tma(const PassArgs a, const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1,
-               unsigned ntiles, int* err) {
+               unsigned ntiles, int* err, unsigned long long limit_ns, unsigned withhold) {
   typedef TmaCfg<P, MODE, NSTAGE> CF;
   constexpr int R1 = P::R1, TT = P::T, N = P::N, NIN = CF::NIN, NS = CF::NS;
   extern __shared__ __align__(1024) unsigned char smem_tma[];
@@ -125,7 +134,7 @@ __global__ void __launch_bounds__(TmaCfg<P, MODE, NSTAGE>::THREADS)
     const int x = (int)(gl0 - o * inner);
     const int y = (int)(o * (unsigned)N);
     float2* dst = stage + (size_t)s * NIN * N * TPW;
-    mbar_expect_tx(&bar[s], CF::TILE_BYTES * NIN);
+    mbar_expect_tx(&bar[s], CF::TILE_BYTES * NIN + withhold);   // withhold > 0: self test only
     tma_load_2d(dst, &tm0, x, y, &bar[s]);
     if constexpr (NIN == 2) tma_load_2d(dst + N * TPW, &tm1, x, y, &bar[s]);
   };
@@ -138,7 +147,7 @@ __global__ void __launch_bounds__(TmaCfg<P, MODE, NSTAGE>::THREADS)
   unsigned k = 0;
   for (unsigned it = blockIdx.x; it < ntiles; it += gridDim.x, ++k) {
     const int s = (int)(k % NS);
-    const bool got = mbar_wait(&bar[s], (k / NS) & 1u);
+    const bool got = mbar_wait(&bar[s], (k / NS) & 1u, limit_ns);
     if (__syncthreads_or(!got)) {
       // a copy did not arrive in time: record it, let the other copies in
       // flight land (bounded), and stop
@@ -146,7 +155,7 @@ __global__ void __launch_bounds__(TmaCfg<P, MODE, NSTAGE>::THREADS)
         atomicExch(err, 1);
         for (unsigned j = 1; j < (unsigned)NS; ++j) {
           const unsigned nx = it + j * gridDim.x;
-          if (nx < ntiles) mbar_wait(&bar[(s + j) % NS], ((k + j) / NS) & 1u);
+          if (nx < ntiles) mbar_wait(&bar[(s + j) % NS], ((k + j) / NS) & 1u, limit_ns);
         }
       }
       return;
@@ -239,8 +248,13 @@ bool encode_array(CUtensorMap* map, const void* base, unsigned inner, unsigned r
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// time limit of a wait for a tile in normal operation (a tile lands in
+// microseconds)
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
 template <class P, int MODE, int NSTAGE>
-cudaError_t pass_tma_p(const PassArgs& a, int* err, cudaStream_t st) {
+cudaError_t pass_tma_p(const PassArgs& a, int* err, cudaStream_t st, unsigned long long limit_ns = kWaitNs,
+                       unsigned withhold = 0) {
   typedef TmaCfg<P, MODE, NSTAGE> CF;
   const unsigned inner = (unsigned)a.g.Itot;
   const unsigned rows = (unsigned)(a.g.lines / a.g.Itot) * (unsigned)P::N;
@@ -268,9 +282,10 @@ cudaError_t pass_tma_p(const PassArgs& a, int* err, cudaStream_t st) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const unsigned grid = std::min<unsigned>(ntiles, (unsigned)(nsm * bps));
 #ifndef BTMV_NO_PDL
-  return launch_pdl(k_pass_tma<P, MODE, NSTAGE>, dim3(grid), dim3(CF::THREADS), sm, st, a, m0, m1, ntiles, err);
+  return launch_pdl(k_pass_tma<P, MODE, NSTAGE>, dim3(grid), dim3(CF::THREADS), sm, st, a, m0, m1, ntiles, err,
+                    limit_ns, withhold);
 #else
-  k_pass_tma<P, MODE, NSTAGE><<<grid, CF::THREADS, sm, st>>>(a, m0, m1, ntiles, err);
+  k_pass_tma<P, MODE, NSTAGE><<<grid, CF::THREADS, sm, st>>>(a, m0, m1, ntiles, err, limit_ns, withhold);
   return cudaGetLastError();
 #endif
 }
@@ -304,6 +319,51 @@ bool pass_tma_supported(int mode, const PassArgs& a, size_t esz) {
   return encode_fn() != nullptr;
 }
 
+// Self test of the bounded waits: one forward-split tile of 32-point lines
+// (16 lines) whose mbarrier is told to expect 16 bytes more than the copy
+// delivers, so that its phase never completes and the wait expires after
+// timeout_ms.  The copy itself lands; nothing faults.  Returns 1 if the
+// kernel reported the expired wait, 0 if not, -1 on a CUDA error.
+static int pass_tma_selftest(int timeout_ms, cudaStream_t st) {
+  if (!encode_fn()) return -1;
+  const int N = 32, inner = TPW;
+  const size_t bytes = (size_t)N * inner * sizeof(float2);
+  void *in = nullptr, *out = nullptr, *tabs = nullptr;
+  int* err_h = nullptr;
+  int* err_d = nullptr;
+  int result = -1;
+  do {
+    if (cudaMalloc(&in, bytes) != cudaSuccess || cudaMalloc(&out, bytes) != cudaSuccess) break;
+    if (cudaMalloc(&tabs, 2 * N * sizeof(float2)) != cudaSuccess) break;
+    if (cudaMemsetAsync(in, 0, bytes, st) != cudaSuccess) break;
+    if (cudaMemsetAsync(tabs, 0, 2 * N * sizeof(float2), st) != cudaSuccess) break;
+    if (cudaHostAlloc((void**)&err_h, sizeof(int), cudaHostAllocMapped) != cudaSuccess) break;
+    *err_h = 0;
+    if (cudaHostGetDevicePointer((void**)&err_d, err_h, 0) != cudaSuccess) break;
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.g.N = N; a.g.ni = 1; a.g.I[0] = inner; a.g.Itot = inner; a.g.lines = inner; a.g.TL = TPW; a.g.halves = 1;
+    ArrMap m;
+    memset(&m, 0, sizeof m);
+    m.os = (long long)N * inner; m.is[0] = 1; m.es = inner; m.len = N;
+    m.vI[0] = m.vI[1] = m.vI[2] = 1 << 30;
+    a.a_in0 = a.a_in1 = a.a_out0 = a.a_out1 = m;
+    a.in0 = in; a.out0 = out;
+    a.fft.N = N;
+    a.fft.tw = (const unsigned char*)tabs;
+    a.fft.ph = (const unsigned char*)tabs + N * sizeof(float2);
+    if (pass_tma_p<RP32, 0, 1>(a, err_d, st, (unsigned long long)timeout_ms * 1000000ull, 16) != cudaSuccess) break;
+    if (cudaStreamSynchronize(st) != cudaSuccess) break;
+    result = *(volatile int*)err_h ? 1 : 0;
+  } while (false);
+  cudaStreamSynchronize(st);
+  if (in) cudaFree(in);
+  if (out) cudaFree(out);
+  if (tabs) cudaFree(tabs);
+  if (err_h) cudaFreeHost(err_h);
+  return result;
+}
+
 cudaError_t launch_pass_tma(int mode, const PassArgs& a, int* err, cudaStream_t st) {
   if (mode == 1 && !a.in1) return cudaErrorInvalidValue;
   switch (a.g.N) {
@@ -316,3 +376,16 @@ cudaError_t launch_pass_tma(int mode, const PassArgs& a, int* err, cudaStream_t 
 }
 
 }  // namespace btmv
+
+void btmv_clear_error();
+btmv_status btmv_set_error(btmv_status st, const char* msg);
+
+extern "C" BTMV_API btmv_status btmv_selftest_tma_timeout(int timeout_ms, void* stream) {
+  btmv_clear_error();
+  if (timeout_ms < 1 || timeout_ms > 10000)
+    return btmv_set_error(BTMV_E_ARG, "selftest_tma_timeout: timeout_ms outside [1, 10000]");
+  const int r = btmv::pass_tma_selftest(timeout_ms, (cudaStream_t)stream);
+  if (r < 0) return btmv_set_error(BTMV_E_CUDA, "selftest_tma_timeout: CUDA error or no tensor-map encoder");
+  if (r == 0) return btmv_set_error(BTMV_E_STATE, "selftest_tma_timeout: the withheld wait was not reported");
+  return btmv_set_error(BTMV_E_TIMEOUT, "selftest_tma_timeout: expired wait reported (expected)");
+}

@@ -313,6 +313,20 @@ def test_tma_staged_passes(n, c, monkeypatch):
     assert np.array_equal(y0, y1)
 
 
+def test_tma_pass_wait_limit_reports_timeout_and_context_survives():
+    """A TMA-staged pass whose mbarrier is told to expect more bytes than the
+    copy delivers gives up its wait after the limit and reports it (no
+    fault); afterwards a split apply whose merges take the TMA-staged kernel
+    (256-point lines) still matches the FP64 oracle."""
+    st = bt.btmv_selftest_tma_timeout(50)
+    assert st == bt.BTMV_E_TIMEOUT, bt.btmv_last_error()
+    n, c = (256, 16), 3
+    t = W.random_generator(n, c, seed=411)
+    x = W.random_vector(n, c, seed=412)
+    y = run_btmv(t, x, n, c, 0, 0)
+    assert rel(y, OE.embed_matvec(t, round_input(x, 0))) <= 1e-5
+
+
 def test_plan_clone_shares_the_symbol():
     n, c = (10, 12, 8), 3
     t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
