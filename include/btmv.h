@@ -106,12 +106,20 @@ enum {
                                       nrhs contraction on tensor cores (c = 3,
                                       complex64, nrhs >= 2): TF32 mma with a
                                       high/low split, FP32 accumulation        */
-  BTMV_FLAG_TWO_STREAMS = 1u << 4  /* split, d >= 3: run the two top-level
+  BTMV_FLAG_TWO_STREAMS = 1u << 4, /* split, d >= 3: run the two top-level
                                       subtrees of Algorithm 1 on two streams
                                       (the caller's and a plan stream) so the
                                       passes of one overlap the leaves of the
                                       other; costs d-2 more workspace vectors
                                       (peak d+1 -> 2d-1 vectors)              */
+  BTMV_FLAG_FUSED_LEVELS = 1u << 5 /* split, d = 3, c = 3, complex64, block-
+                                      symmetric compressed store, n_1 = n_2 =
+                                      64: the last two levels of Algorithm 1
+                                      (the dim-1 split, the leaf, the dim-1
+                                      merge) run as one kernel per level-1
+                                      node, its n_1 x n_2 slabs held in shared
+                                      memory (Sec. II.B); other plans ignore
+                                      the flag                                */
 };
 
 /*
@@ -369,7 +377,8 @@ enum {
   BTMV_K_FULL_LEAF = 4,    /* full embedding: last-dim forward+multiply+inverse */
   BTMV_K_FULL_INV = 5,     /* full embedding: inverse passes (+ projection)    */
   BTMV_K_COPY = 6,         /* host staging copies                              */
-  BTMV_K_NKINDS = 7
+  BTMV_K_FUSED_LEVELS = 7, /* two fused levels (BTMV_FLAG_FUSED_LEVELS)       */
+  BTMV_K_NKINDS = 8
 };
 
 /*

@@ -24,8 +24,8 @@ BTMV_C64, BTMV_C128 = 0, 1
 BTMV_ALGO_SPLIT, BTMV_ALGO_FULL, BTMV_ALGO_FULL_CUFFT = 0, 1, 2
 BTMV_SYM_NONE, BTMV_SYM_BLOCK, BTMV_SYM_PARITY, BTMV_SYM_ADJOINT = 0, 1, 2, 4
 BTMV_FLAG_NONE, BTMV_FLAG_PROFILE, BTMV_FLAG_GENERIC, BTMV_FLAG_SHARED_RHS, BTMV_FLAG_TENSOR_CORE = 0, 1, 2, 4, 8
-BTMV_FLAG_TWO_STREAMS = 16
-KINDS = ["fwd_split", "leaf", "merge", "full_fwd", "full_leaf", "full_inv", "copy"]
+BTMV_FLAG_TWO_STREAMS, BTMV_FLAG_FUSED_LEVELS = 16, 32
+KINDS = ["fwd_split", "leaf", "merge", "full_fwd", "full_leaf", "full_inv", "copy", "fused_levels"]
 BTMV_K_NKINDS = len(KINDS)
 
 

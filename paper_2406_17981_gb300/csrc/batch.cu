@@ -182,6 +182,7 @@ btmv_status build_stages(const Entry& e, const TuneCfg& cfg, std::vector<BatchSt
       if (sl >= steps[i].size()) continue;
       const Step& s = steps[i][sl];
       const btmv_plan p = e.plans[i];
+      if (s.kind > 2) return fail(BTMV_E_STATE, "batch: step kind %d has no batched form", s.kind);
       BatchStage bs;
       memset(&bs, 0, sizeof bs);
       bs.kind = s.kind;

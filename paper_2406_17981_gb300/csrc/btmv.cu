@@ -214,7 +214,7 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
     return fail(BTMV_E_ARG, "plan_create: bad algo %d", algo);
   if (max_rhs < 1) return fail(BTMV_E_ARG, "plan_create: max_rhs=%d < 1", max_rhs);
   if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC | BTMV_FLAG_SHARED_RHS | BTMV_FLAG_TENSOR_CORE |
-                          BTMV_FLAG_TWO_STREAMS))
+                          BTMV_FLAG_TWO_STREAMS | BTMV_FLAG_FUSED_LEVELS))
     return fail(BTMV_E_ARG, "plan_create: unknown flags 0x%x", flags);
   if (algo == BTMV_ALGO_FULL && d > 4)
     return fail(BTMV_E_UNSUPPORTED, "plan_create: the plain embedding takes d <= 4 (d=%d)", d);
@@ -295,7 +295,7 @@ extern "C" btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flag
   *out = nullptr;
   if (max_rhs < 1) return fail(BTMV_E_ARG, "plan_clone: max_rhs=%d < 1", max_rhs);
   if (flags & ~(uint32_t)(BTMV_FLAG_PROFILE | BTMV_FLAG_GENERIC | BTMV_FLAG_SHARED_RHS | BTMV_FLAG_TENSOR_CORE |
-                          BTMV_FLAG_TWO_STREAMS))
+                          BTMV_FLAG_TWO_STREAMS | BTMV_FLAG_FUSED_LEVELS))
     return fail(BTMV_E_ARG, "plan_clone: unknown flags 0x%x", flags);
   btmv_plan p = new btmv_plan_s();
   p->d = src->d; p->c = src->c; p->prec = src->prec; p->algo = src->algo; p->max_rhs = max_rhs; p->flags = flags;
@@ -765,32 +765,44 @@ static btmv_status leaf_launch(btmv_plan p, int nrhs, int nn, const LeafNode* no
 // Depth-first traversal of Algorithm 1 (see btmv_apply in btmv.h): a node at
 // level m (transformed along dims 0..m-1) is split along dim m into itself
 // (even half) and W[m] (odd half); at the last split level both children go
-// to one leaf launch; merges run on the way back up.
+// to one leaf launch; merges run on the way back up.  With fuse, a node at
+// level d-2 is one kind-3 step instead (its split, leaf and merge in one
+// kernel, W[d-2] as scratch).
 static void split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, std::vector<Step>& out,
-                           const std::vector<void*>& W);
+                           const std::vector<void*>& W, bool fuse);
 
 static void split_descend(btmv_plan p, int m, void* buf, int prefix, std::vector<Step>& out,
-                          const std::vector<void*>& W) {
+                          const std::vector<void*>& W, bool fuse) {
   void* Wm = W[m];
+  if (fuse && m == p->d - 2) {
+    Step z = {3, m, buf, nullptr, buf, Wm, 1, {{buf, buf, prefix}}};
+    out.push_back(z);
+    return;
+  }
   Step f = {0, m, buf, nullptr, buf, Wm, 0, {}};
   out.push_back(f);
-  split_children(p, m, buf, Wm, prefix, prefix | (1 << m), out, W);
+  split_children(p, m, buf, Wm, prefix, prefix | (1 << m), out, W, fuse);
   Step g = {1, m, buf, Wm, buf, nullptr, 0, {}};
   out.push_back(g);
 }
 
 static void split_children(btmv_plan p, int m, void* e, void* o, int pe, int po, std::vector<Step>& out,
-                           const std::vector<void*>& W) {
+                           const std::vector<void*>& W, bool fuse) {
   if (m + 1 == p->d - 1) {
     Step l = {2, p->d - 1, nullptr, nullptr, nullptr, nullptr, 2, {{e, e, pe}, {o, o, po}}};
     out.push_back(l);
     return;
   }
-  split_descend(p, m + 1, e, pe, out, W);
-  split_descend(p, m + 1, o, po, out, W);
+  split_descend(p, m + 1, e, pe, out, W, fuse);
+  split_descend(p, m + 1, o, po, out, W, fuse);
 }
 
-void btmv::split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& out) {
+bool btmv::two_level_fusable(btmv_plan p) {
+  if (!(p->flags & BTMV_FLAG_FUSED_LEVELS) || p->algo != BTMV_ALGO_SPLIT || p->prec != BTMV_C64) return false;
+  return fuse2_supported(p->d, p->c, p->n, sizeof(float2), p->symdev);
+}
+
+void btmv::split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& out, bool fuse) {
   out.clear();
   if (p->d == 1) {
     Step l = {2, 0, nullptr, nullptr, nullptr, nullptr, 1, {{x, y, 0}, {}}};
@@ -799,16 +811,27 @@ void btmv::split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& o
   }
   Step f = {0, 0, x, nullptr, y, p->W[0], 0, {}};
   out.push_back(f);
-  split_children(p, 0, y, p->W[0], 0, 1, out, p->W);
+  split_children(p, 0, y, p->W[0], 0, 1, out, p->W, fuse);
   Step g = {1, 0, y, p->W[0], y, nullptr, 0, {}};
   out.push_back(g);
+}
+
+// The kind-3 step: one fused kernel for the node's last two levels.
+static btmv_status fused_levels(btmv_plan p, const Step& s, int nrhs, cudaStream_t st) {
+  ProfScope ps(p, BTMV_K_FUSED_LEVELS, st);
+  const int m = s.dim;
+  cudaError_t e = launch_fuse2((float2*)s.out0, (float2*)s.out1, s.nodes[0].prefix, p->n[0], nrhs,
+                               p->fft_apply[m], p->fft_apply[m + 1], p->symdev, st);
+  if (e != cudaSuccess) return fail(BTMV_E_CUDA, "fused levels: %s", cudaGetErrorString(e));
+  return BTMV_OK;
 }
 
 template <class T>
 static btmv_status run_steps(btmv_plan p, const std::vector<Step>& steps, int nrhs, cudaStream_t st) {
   for (const Step& s : steps) {
-    if (s.kind == 2) TRY(leaf_launch<T>(p, nrhs, s.nn, s.nodes, false, st));
-    else             TRY(split_pass<T>(p, s, nrhs, st));
+    if (s.kind == 2)      TRY(leaf_launch<T>(p, nrhs, s.nn, s.nodes, false, st));
+    else if (s.kind == 3) TRY(fused_levels(p, s, nrhs, st));
+    else                  TRY(split_pass<T>(p, s, nrhs, st));
   }
   return BTMV_OK;
 }
@@ -816,8 +839,9 @@ static btmv_status run_steps(btmv_plan p, const std::vector<Step>& steps, int nr
 template <class T>
 static btmv_status split_apply(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
   std::vector<Step> steps;
+  const bool fuse = two_level_fusable(p);
   if (!p->side) {
-    split_steps(p, x, y, steps);
+    split_steps(p, x, y, steps, fuse);
     return run_steps<T>(p, steps, nrhs, st);
   }
   // two top-level subtrees on two streams: the even one on st with W, the
@@ -832,8 +856,8 @@ static btmv_status split_apply(btmv_plan p, const void* x, void* y, int nrhs, cu
     Step l = {2, 1, nullptr, nullptr, nullptr, nullptr, 2, {{y, y, 0}, {p->W[0], p->W[0], 1}}};
     a.push_back(l);
   } else {
-    split_descend(p, 1, y, 0, a, p->W);
-    split_descend(p, 1, p->W[0], 1, b, p->W2);
+    split_descend(p, 1, y, 0, a, p->W, fuse);
+    split_descend(p, 1, p->W[0], 1, b, p->W2, fuse);
   }
   TRY(run_steps<T>(p, a, nrhs, st));
   TRY(run_steps<T>(p, b, nrhs, p->side));
@@ -1060,8 +1084,13 @@ static int launches_per_apply(btmv_plan p) {
   const int d = p->d;
   if (p->algo == BTMV_ALGO_SPLIT) {
     if (d == 1) return 1;
-    // forward + merge per internal node of levels 0..d-2, one leaf launch per level-(d-2) node
     int n = 0;
+    if (two_level_fusable(p)) {
+      // forward + merge per node of levels 0..d-3, one fused launch per level-(d-2) node
+      for (int m = 0; m < d - 2; ++m) n += 2 * (1 << m);
+      return n + (1 << (d - 2));
+    }
+    // forward + merge per internal node of levels 0..d-2, one leaf launch per level-(d-2) node
     for (int m = 0; m < d - 1; ++m) n += 2 * (1 << m);
     n += 1 << (d - 2);
     return n;

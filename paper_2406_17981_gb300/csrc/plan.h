@@ -103,7 +103,9 @@ namespace btmv {
 
 // One launch of the depth-first schedule of Algorithm 1.
 struct Step {
-  int kind;            // 0 forward split pass, 1 merge pass, 2 leaf
+  int kind;            // 0 forward split pass, 1 merge pass, 2 leaf,
+                       // 3 the last two levels fused (node in0/out0, scratch out1,
+                       // parity prefix nodes[0].prefix; per-call launcher only)
   int dim;             // level (dimension) of a pass
   const void* in0;
   const void* in1;
@@ -116,8 +118,16 @@ struct Step {
 btmv_status fail(btmv_status st, const char* fmt, ...);
 // Radix factorisation of N into stages: mode 0 prefers radix 16, mode 1 radix 8.
 bool factor_radices_mode(int N, FftDev& f, int mode);
-// Steps of one split apply on device pointers (d >= 1).
-void split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& out);
+// Steps of one split apply on device pointers (d >= 1); fuse: the last two
+// levels as kind-3 steps where two_level_fusable(p).
+void split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& out, bool fuse = false);
+// BTMV_FLAG_FUSED_LEVELS is set and the plan's shape has a fused kernel.
+bool two_level_fusable(btmv_plan p);
+// The fused last two levels (fused2.cu): d = 3, c = 3, complex64, block-
+// symmetric compressed store, n_1 = n_2 = 64.
+bool fuse2_supported(int d, int c, const int* n, size_t esz, const SymDev& S);
+cudaError_t launch_fuse2(float2* node, float2* scratch, int prefix0, int n0, int nrhs, const FftDev& f1,
+                         const FftDev& f2, const SymDev& sym, cudaStream_t st);
 // Arguments of a split pass step; TL = 0 picks the default tile.
 PassArgs split_pass_args(btmv_plan p, const Step& s, int nrhs, size_t esz, int TL);
 // Arguments of a leaf step; Lt, rq = 0 pick the defaults.

@@ -14,12 +14,12 @@ def round_input(x, precision):
     return x.astype(dt).astype(np.complex128)
 
 
-def run_btmv(t, x, n, c, precision, algo=0, sym_flags=0, parity=None, nrhs=None, host=False):
+def run_btmv(t, x, n, c, precision, algo=0, sym_flags=0, parity=None, nrhs=None, host=False, flags=0):
     import torch
 
     from paper_2406_17981_gb300 import btmv as bt
     nrhs = x.shape[0] if nrhs is None else nrhs
-    plan = bt.Plan(n, c, precision, algo, max_rhs=max(1, nrhs))
+    plan = bt.Plan(n, c, precision, algo, max_rhs=max(1, nrhs), flags=flags)
     try:
         plan.set_kernel(t, sym_flags, parity)
         dt = np.complex64 if precision == 0 else np.complex128

@@ -60,3 +60,46 @@ def test_null_plan_calls_fail_cleanly(L):
     assert L.btmv_apply_batched(0, None, None, None, None, None) == bt.BTMV_OK
     assert L.btmv_apply_batched(-1, None, None, None, None, None) == bt.BTMV_E_ARG
     assert L.btmv_plan_get_info(None, None) == bt.BTMV_E_ARG
+
+
+def _header_enums():
+    """NAME = value pairs of the header's enums (integers and 1u << k)."""
+    import re
+    text = open(bt.HEADER).read()
+    out = {}
+    for name, val in re.findall(r"^\s*(BTMV_[A-Z0-9_]+)\s*=\s*([0-9u<\s]+?)\s*[,/\n]", text, re.M):
+        val = val.replace("u", "").strip()
+        out[name] = (1 << int(val.split("<<")[1])) if "<<" in val else int(val)
+    return out
+
+
+def test_binding_constants_match_header():
+    """Every enum constant the Python binding defines has the header's value,
+    and the profile kinds are in the header's order."""
+    enums = _header_enums()
+    assert enums["BTMV_FLAG_FUSED_LEVELS"] == 32 and enums["BTMV_K_NKINDS"] == len(bt.KINDS)
+    checked = 0
+    for name, val in enums.items():
+        if hasattr(bt, name):
+            assert getattr(bt, name) == val, name
+            checked += 1
+    assert checked >= 20
+    kinds = sorted((v, k) for k, v in enums.items() if k.startswith("BTMV_K_") and k != "BTMV_K_NKINDS")
+    assert [k[len("BTMV_K_"):].lower() for _, k in kinds] == bt.KINDS
+
+
+def test_plan_create_accepts_every_declared_flag(L):
+    """Plan flags declared in the header are accepted (the plan is created
+    on the host side only when no device is present: creation fails there
+    with a CUDA status, not BTMV_E_ARG)."""
+    enums = _header_enums()
+    flags = 0
+    for name, val in enums.items():
+        if name.startswith("BTMV_FLAG_"):
+            flags |= val
+    try:
+        h = bt.btmv_plan_create(1, [4], 1, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, 1, flags)
+    except bt.BtmvError as e:
+        assert e.status != bt.BTMV_E_ARG, bt.btmv_last_error()
+    else:
+        bt.btmv_destroy(h)

@@ -538,3 +538,83 @@ def test_padded_green_parity_and_adjoint(n):
     lhs = np.vdot(z, yf)
     rhs = np.vdot(yz, x)
     assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(yf) * np.linalg.norm(z)
+
+
+FUSED_CASES = [((1, 64, 64), "green", 1), ((3, 64, 64), "green", 2), ((7, 64, 64), "skew", 3),
+               ((16, 64, 64), "green", 1), ((5, 64, 64), "skew", 1)]
+
+
+def _fused_instance(n, kind, nrhs):
+    if kind == "skew":
+        t_orth, par = W.skew_orthant(n, seed=95, c=3)
+    else:
+        t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    x = W.random_vector(n, 3, seed=96, nrhs=nrhs)
+    return t_orth, par, x
+
+
+@pytest.mark.parametrize("n,kind,nrhs", FUSED_CASES)
+@pytest.mark.parametrize("streams", [0, 1])
+def test_fused_two_levels(n, kind, nrhs, streams):
+    """The last two levels of Algorithm 1 as one kernel per level-1 node
+    (dim-1 split, leaf along dim 2, dim-1 merge on a shared-memory slab)
+    against the FP64 oracle and the unfused schedule, with and without the
+    two-stream traversal; the fused plan launches 4 kernels per apply."""
+    t_orth, par, x = _fused_instance(n, kind, nrhs)
+    flags = bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY
+    extra = bt.BTMV_FLAG_TWO_STREAMS if streams else 0
+    ref = OE.embed_matvec(W.orthant_to_full(t_orth, par), round_input(x, 0))
+    y0 = run_btmv(t_orth, x, n, 3, 0, 0, flags, par, flags=extra)
+    y1 = run_btmv(t_orth, x, n, 3, 0, 0, flags, par, flags=extra | bt.BTMV_FLAG_FUSED_LEVELS)
+    assert rel(y1, ref) <= 1e-5
+    assert rel(y1, y0) <= 1e-6
+    plan = bt.Plan(n, 3, 0, max_rhs=nrhs, flags=bt.BTMV_FLAG_FUSED_LEVELS)
+    try:
+        plan.set_kernel(t_orth, flags, par)
+        assert plan.info["launches_per_apply"] == 4
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("n,c,sym", [((4, 32, 32), 3, 3), ((4, 64, 64), 1, 0), ((4, 64, 64), 3, 0),
+                                     ((2, 64, 64, 8), 3, 3), ((4, 64, 128), 3, 3)])
+def test_fused_flag_ignored_elsewhere(n, c, sym):
+    """Plans without a fused kernel (other sizes, c = 1, the full store,
+    d = 4) run the unfused schedule under BTMV_FLAG_FUSED_LEVELS."""
+    if sym and len(n) == 3:
+        t, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    elif sym:
+        t, par = W.skew_orthant(n, seed=97, c=3)
+    else:
+        t, par = W.random_generator(n, c, seed=97), None
+    x = W.random_vector(n, c, seed=98, nrhs=1)
+    full = W.orthant_to_full(t, par) if par is not None else t
+    ref = OE.embed_matvec(full, round_input(x, 0))
+    y = run_btmv(t, x, n, c, 0, 0, sym, par, flags=bt.BTMV_FLAG_FUSED_LEVELS)
+    assert rel(y, ref) <= 1e-5
+    plan = bt.Plan(n, c, 0, max_rhs=1, flags=bt.BTMV_FLAG_FUSED_LEVELS)
+    try:
+        plan.set_kernel(t, sym, par)
+        d = len(n)
+        assert plan.info["launches_per_apply"] == sum(2 << m for m in range(d - 1)) + (1 << (d - 2))
+    finally:
+        plan.close()
+
+
+def test_fused_two_levels_profile():
+    """BTMV_FLAG_PROFILE reports the fused launches under their own kind."""
+    n = (4, 64, 64)
+    t_orth, par, x = _fused_instance(n, "green", 1)
+    plan = bt.Plan(n, 3, 0, max_rhs=1, flags=bt.BTMV_FLAG_FUSED_LEVELS | bt.BTMV_FLAG_PROFILE)
+    try:
+        plan.set_kernel(t_orth, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+        xd = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+        yd = torch.zeros_like(xd)
+        bt.btmv_profile_read(plan.handle)
+        plan.apply(xd, yd, 1)
+        prof = bt.btmv_profile_read(plan.handle)
+        assert prof["fused_levels"][1] == 2
+        assert prof["leaf"][1] == 0
+        assert prof["fwd_split"][1] == 1 and prof["merge"][1] == 1
+    finally:
+        plan.close()
