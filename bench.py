@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS) + ["batched64", "serving200", "multirhs", "cpu_fig3"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS) + ["batched64", "serving200", "multirhs", "cpu_fig3",
+                                                                  "fused_levels"])
     ap.add_argument("--no-compare", action="store_true", help="skip the full-embedding and cuFFT rows")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle timing")
     ap.add_argument("--no-secondary", action="store_true",
@@ -88,6 +89,7 @@ KERNEL_SOURCES = {
     "leaf": ["fast_leaf.cu", "fast_leaf3.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
     "fwd_split": ["fast_pass.cu", "fast_pass_tma.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
     "merge": ["fast_pass.cu", "fast_pass_tma.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
+    "fused2": ["fused2.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
 }
 
 
@@ -259,9 +261,9 @@ def run_reference(args, cfg):
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
-    if args.workload in ("batched64", "serving200", "multirhs", "cpu_fig3"):
+    if args.workload in ("batched64", "serving200", "multirhs", "cpu_fig3", "fused_levels"):
         fn = {"batched64": run_batched, "serving200": run_serving, "multirhs": run_multirhs,
-              "cpu_fig3": run_cpu_fig3}[args.workload]
+              "cpu_fig3": run_cpu_fig3, "fused_levels": run_fused_levels}[args.workload]
         line = fn(args)
         if line is not None:
             print(json.dumps(line))
@@ -591,6 +593,12 @@ def secondaries(args):
     except Exception as ex:
         out["serving200"] = {"error": str(ex)[:300]}
     out["serving200"]["wall_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    try:
+        out["fused_levels"] = run_fused_levels(argparse.Namespace(**vars(args)), dist=False)
+    except Exception as ex:
+        out["fused_levels"] = {"error": str(ex)[:300]}
+    out["fused_levels"]["wall_s"] = time.perf_counter() - t0
     del bt
     return out
 
@@ -750,6 +758,100 @@ def run_multirhs(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": {"workload": "multirhs", "nrhs": 16}, "variants": out}
     return line
+
+
+FUSED_N, FUSED_RHS = (512, 64, 64), 8
+
+
+def run_fused_levels(args, dist=True):
+    """The d = 3 split apply with its last two levels fused into one kernel
+    per level-1 node (BTMV_FLAG_FUSED_LEVELS) against the unfused schedule,
+    each with one and two streams: n = 512 x 64 x 64, c = 3 Green, complex64,
+    8 right-hand sides (each vector 403 MB, past L2).  Rates count
+    right-hand-side matvecs per second; the fused kernel's launch time comes
+    from the plan's profile events and its algorithmic bytes from
+    analysis.fused_pass_bytes (node read and written, symbol once per apply,
+    so half of it per launch)."""
+    import torch
+
+    from paper_2406_17981_gb300 import analysis as A
+    from paper_2406_17981_gb300 import btmv as bt
+    ws, rank, local = dist_setup(args) if dist else (1, 0, 0)
+    n, r = FUSED_N, FUSED_RHS
+    steps = max(5, min(args.steps, 100))
+    t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    xc = W.random_vector(n, 3, seed=37, nrhs=r).astype(np.complex64)
+    x = torch.from_numpy(xc).cuda()
+    out, ys = {}, {}
+    for name, fl in (("unfused", 0), ("fused", bt.BTMV_FLAG_FUSED_LEVELS),
+                     ("unfused_two_streams", bt.BTMV_FLAG_TWO_STREAMS),
+                     ("fused_two_streams", bt.BTMV_FLAG_FUSED_LEVELS | bt.BTMV_FLAG_TWO_STREAMS)):
+        p = bt.Plan(n, 3, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=r, flags=fl)
+        p.set_kernel(t_orth, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+        y = torch.empty_like(x)
+        ms = time_plan_apply_rhs(p, x, y, r, steps)
+        ys[name] = y
+        out[name] = {"rhs_matvecs_per_s": r * 1000.0 / ms, "ms_per_step": ms,
+                     "launches_per_apply": p.info["launches_per_apply"]}
+        sym_bytes = p.info["symbol_bytes"]
+        p.close()
+    # the fused kernel alone: profile events around each launch
+    p = bt.Plan(n, 3, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=r,
+                flags=bt.BTMV_FLAG_FUSED_LEVELS | bt.BTMV_FLAG_PROFILE)
+    p.set_kernel(t_orth, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+    y = torch.empty_like(x)
+    time_plan_apply_rhs(p, x, y, r, 1)
+    bt.btmv_profile_read(p.handle)
+    for _ in range(5):
+        p.apply(x, y, r)
+    prof = bt.btmv_profile_read(p.handle)
+    p.close()
+    fb = A.fused_pass_bytes(n, 3, r, 8, sym_bytes)
+    per_launch = fb["fused_levels"] / 2
+    us = 1000 * prof["fused_levels"][0] / max(1, prof["fused_levels"][1])
+    peak = float(measured_peaks()[0]["hbm_gbs"])
+    out["fused_kernel"] = {"avg_us": us, "launches": prof["fused_levels"][1], "algo_bytes_per_launch": per_launch,
+                           "algo_GBps": per_launch / us / 1e3, "frac_of_measured_hbm": per_launch / us / 1e3 / peak,
+                           "share_of_apply": prof["fused_levels"][0] / max(1e-12, sum(v[0] for v in prof.values())),
+                           "traffic": ncu_traffic("fused2", "d3_512x64x64_c3_green_c64")}
+    out["speedup_fused_vs_unfused"] = out["unfused"]["ms_per_step"] / out["fused"]["ms_per_step"]
+    out["speedup_fused_vs_unfused_two_streams"] = (out["unfused_two_streams"]["ms_per_step"] /
+                                                   out["fused_two_streams"]["ms_per_step"])
+    yf = ys["fused"].cpu().numpy().astype(np.complex128)
+    yu = ys["unfused"].cpu().numpy().astype(np.complex128)
+    out["rel_l2_fused_vs_unfused"] = float(np.linalg.norm(yf - yu) / np.linalg.norm(yu))
+    if not args.no_cpu:
+        from oracle import toeplitz as OT
+        rng = np.random.default_rng(41)
+        pts = [tuple(int(v) for v in rng.integers(0, n)) for _ in range(6)]
+        vals = OT.direct_points(W.orthant_to_full(t_orth, par), xc[:1].astype(np.complex128), pts)
+        got = np.stack([yf[(0, slice(None)) + q] for q in pts])
+        out["rel_l2_vs_fp64_direct_sum_sampled"] = float(np.linalg.norm(got - vals[:, 0]) /
+                                                         np.linalg.norm(vals[:, 0]))
+    if rank != 0 or not dist:
+        return out
+    return {"metric": "block Toeplitz rhs-matvecs/s, last two levels fused (d=3 c=3 Green 512x64x64, 8 rhs, complex64)",
+            "value": out["fused"]["rhs_matvecs_per_s"], "unit": "matvecs/s", "n_gpus": ws, "steps": steps,
+            "warmup": 3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "fused_levels", "n": list(n), "nrhs": r,
+                                            "l2": "inputs larger than L2"},
+            "variants": out}
+
+
+def time_plan_apply_rhs(plan, x, y, nrhs, steps):
+    """Mean ms of `steps` applies with nrhs right-hand sides (after 3 warm-up applies)."""
+    import torch
+    for _ in range(3):
+        plan.apply(x, y, nrhs)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.apply(x, y, nrhs)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
 
 
 def run_cpu_fig3(args):

@@ -100,6 +100,22 @@ def split_pass_bytes(n, c: int, nrhs: int, elem_bytes: int, sym_bytes: int) -> d
             "total": fwd + leaf + mrg, "V": V}
 
 
+def fused_pass_bytes(n, c: int, nrhs: int, elem_bytes: int, sym_bytes: int) -> dict:
+    """Algorithmic bytes of a d = 3 split apply with the last two levels
+    fused (BTMV_FLAG_FUSED_LEVELS): the dim-0 split reads x and writes both
+    level-1 nodes (3V), each fused launch reads its node and writes it back
+    (2V; the levels below it stay on chip), the symbol is read once, and the
+    dim-0 merge reads both nodes and writes y (3V).  The fused kernel's
+    scratch vector (the even half of the dim-1 merge parked off chip) is an
+    implementation cost, not counted here."""
+    if len(n) != 3:
+        raise ValueError("the fused schedule is d = 3")
+    V = vector_bytes(n, c, nrhs, elem_bytes)
+    fused = 2 * 2 * V + sym_bytes
+    return {"fwd_split": 3 * V, "fused_levels": fused, "bwd_merge": 3 * V,
+            "total": 6 * V + fused, "V": V}
+
+
 def full_pass_bytes(n, c: int, nrhs: int, elem_bytes: int, sym_bytes: int) -> dict:
     """Algorithmic bytes of the plain full embedding with the library's own
     kernels: the first pass reads x (V) and writes the zero-padded,

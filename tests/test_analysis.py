@@ -50,3 +50,18 @@ def test_split_traffic_model_d3():
     assert A.split_pass_bytes((8, 8), 1, 1, 8, 0)["total"] == 10 * V2
     V1 = A.vector_bytes((8,), 1, 1, 8)
     assert A.split_pass_bytes((8,), 1, 1, 8, 0)["total"] == 2 * V1
+
+
+def test_fused_pass_bytes_drop_the_inner_levels():
+    """Fusing the last two levels of a d = 3 apply removes the dim-1 split,
+    the leaf's separate reads and writes and the dim-1 merge: 26 V -> 10 V
+    (plus the symbol once in both)."""
+    n, c, S = (16, 64, 64), 3, 12345
+    V = 16 * 64 * 64 * 3 * 8
+    split = A.split_pass_bytes(n, c, 1, 8, S)
+    fused = A.fused_pass_bytes(n, c, 1, 8, S)
+    assert split["total"] == 26 * V + S
+    assert fused["total"] == 10 * V + S
+    assert fused["fwd_split"] + fused["bwd_merge"] == 6 * V
+    with pytest.raises(ValueError):
+        A.fused_pass_bytes((8, 8), 1, 1, 8, 0)
