@@ -119,7 +119,12 @@ enum {
                                       merge) run as one kernel per level-1
                                       node, its n_1 x n_2 slabs held in shared
                                       memory (Sec. II.B); other plans ignore
-                                      the flag                                */
+                                      the flag.  An apply fuses when its grid
+                                      has at least 4 blocks per SM (nrhs n_0 >=
+                                      4 x SMs; BTMV_FUSE_MIN_BLOCKS=k in the
+                                      environment sets k), else it runs
+                                      unfused; plan info counts launches for
+                                      max_rhs                                 */
 };
 
 /*

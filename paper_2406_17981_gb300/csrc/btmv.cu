@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -248,6 +249,7 @@ extern "C" btmv_status btmv_plan_create(btmv_plan* out, int d, const int32_t* n,
   }
   n = p->n;                        // the padded sizes from here on
   if (cudaGetDevice(&p->dev) != cudaSuccess) { free_plan(p); return fail(BTMV_E_CUDA, "plan_create: no CUDA device"); }
+  cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->dev);
 
   std::vector<int> Nf, Nd;
   for (int m = 0; m < d; ++m) {
@@ -300,7 +302,7 @@ extern "C" btmv_status btmv_plan_clone(btmv_plan src, int max_rhs, uint32_t flag
   btmv_plan p = new btmv_plan_s();
   p->d = src->d; p->c = src->c; p->prec = src->prec; p->algo = src->algo; p->max_rhs = max_rhs; p->flags = flags;
   for (int m = 0; m < MAX_D; ++m) { p->n[m] = src->n[m]; p->fft_apply[m] = src->fft_apply[m]; p->fft_sym[m] = src->fft_sym[m]; }
-  p->s = src->s; p->s2 = src->s2; p->esz = src->esz; p->dev = src->dev;
+  p->s = src->s; p->s2 = src->s2; p->esz = src->esz; p->dev = src->dev; p->nsm = src->nsm;
   for (int m = 0; m < MAX_D; ++m) p->nu[m] = src->nu[m];
   p->su = src->su; p->padded = src->padded;
   p->tab = src->tab;                                  // shared twiddle tables
@@ -802,6 +804,25 @@ bool btmv::two_level_fusable(btmv_plan p) {
   return fuse2_supported(p->d, p->c, p->n, sizeof(float2), p->symdev);
 }
 
+// The fused kernel runs one block per (dim-0 index, right-hand side) and
+// measured slower than the unfused schedule on small grids (64^3 with one
+// right-hand side, 64 blocks: 0.116 against 0.071 ms), level at 512 blocks
+// and 9-13% faster from 1024 blocks (two blocks per SM), so an apply fuses
+// from 4 blocks per SM; BTMV_FUSE_MIN_BLOCKS=k in the environment sets
+// another threshold (0: always).  The kernel copies the node it updates in
+// 16-byte pieces; btmv_apply already requires 16-byte aligned x and y, and
+// the test below keeps any other caller unfused.
+static long long fuse_min_blocks(btmv_plan p) {
+  const char* v = getenv("BTMV_FUSE_MIN_BLOCKS");
+  if (v && *v) return atoll(v);
+  return 4ll * std::max(1, p->nsm);
+}
+
+bool btmv::fuse_this_apply(btmv_plan p, int nrhs, const void* y) {
+  if (!two_level_fusable(p) || ((uintptr_t)y & 15)) return false;
+  return (long long)nrhs * p->n[0] >= fuse_min_blocks(p);
+}
+
 void btmv::split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& out, bool fuse) {
   out.clear();
   if (p->d == 1) {
@@ -839,7 +860,7 @@ static btmv_status run_steps(btmv_plan p, const std::vector<Step>& steps, int nr
 template <class T>
 static btmv_status split_apply(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
   std::vector<Step> steps;
-  const bool fuse = two_level_fusable(p);
+  const bool fuse = fuse_this_apply(p, nrhs, y);
   if (!p->side) {
     split_steps(p, x, y, steps, fuse);
     return run_steps<T>(p, steps, nrhs, st);
@@ -1085,7 +1106,7 @@ static int launches_per_apply(btmv_plan p) {
   if (p->algo == BTMV_ALGO_SPLIT) {
     if (d == 1) return 1;
     int n = 0;
-    if (two_level_fusable(p)) {
+    if (two_level_fusable(p) && (long long)p->max_rhs * p->n[0] >= fuse_min_blocks(p)) {
       // forward + merge per node of levels 0..d-3, one fused launch per level-(d-2) node
       for (int m = 0; m < d - 2; ++m) n += 2 * (1 << m);
       return n + (1 << (d - 2));

@@ -47,6 +47,7 @@ struct btmv_plan_s {
   long long s2 = 1;         // prod 2n
   size_t esz = 8;           // bytes per complex
   int dev = 0;
+  int nsm = 0;              // SMs of dev
   btmv::TableSet tab;
   btmv::FftDev fft_apply[btmv::MAX_D];  // per dim, plan precision (N = n_m split, 2 n_m full)
   btmv::FftDev fft_sym[btmv::MAX_D];    // per dim, FP64, N = n_m
@@ -123,6 +124,9 @@ bool factor_radices_mode(int N, FftDev& f, int mode);
 void split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& out, bool fuse = false);
 // BTMV_FLAG_FUSED_LEVELS is set and the plan's shape has a fused kernel.
 bool two_level_fusable(btmv_plan p);
+// ... and an apply with nrhs right-hand sides into y takes it (grid size and
+// alignment rules of btmv.h).
+bool fuse_this_apply(btmv_plan p, int nrhs, const void* y);
 // The fused last two levels (fused2.cu): d = 3, c = 3, complex64, block-
 // symmetric compressed store, n_1 = n_2 = 64.
 bool fuse2_supported(int d, int c, const int* n, size_t esz, const SymDev& S);

@@ -555,11 +555,13 @@ def _fused_instance(n, kind, nrhs):
 
 @pytest.mark.parametrize("n,kind,nrhs", FUSED_CASES)
 @pytest.mark.parametrize("streams", [0, 1])
-def test_fused_two_levels(n, kind, nrhs, streams):
+def test_fused_two_levels(n, kind, nrhs, streams, monkeypatch):
     """The last two levels of Algorithm 1 as one kernel per level-1 node
     (dim-1 split, leaf along dim 2, dim-1 merge on a shared-memory slab)
     against the FP64 oracle and the unfused schedule, with and without the
-    two-stream traversal; the fused plan launches 4 kernels per apply."""
+    two-stream traversal; the fused plan launches 4 kernels per apply
+    (fusion forced on these small grids)."""
+    monkeypatch.setenv("BTMV_FUSE_MIN_BLOCKS", "0")
     t_orth, par, x = _fused_instance(n, kind, nrhs)
     flags = bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY
     extra = bt.BTMV_FLAG_TWO_STREAMS if streams else 0
@@ -601,8 +603,9 @@ def test_fused_flag_ignored_elsewhere(n, c, sym):
         plan.close()
 
 
-def test_fused_two_levels_profile():
+def test_fused_two_levels_profile(monkeypatch):
     """BTMV_FLAG_PROFILE reports the fused launches under their own kind."""
+    monkeypatch.setenv("BTMV_FUSE_MIN_BLOCKS", "0")
     n = (4, 64, 64)
     t_orth, par, x = _fused_instance(n, "green", 1)
     plan = bt.Plan(n, 3, 0, max_rhs=1, flags=bt.BTMV_FLAG_FUSED_LEVELS | bt.BTMV_FLAG_PROFILE)
@@ -616,5 +619,36 @@ def test_fused_two_levels_profile():
         assert prof["fused_levels"][1] == 2
         assert prof["leaf"][1] == 0
         assert prof["fwd_split"][1] == 1 and prof["merge"][1] == 1
+    finally:
+        plan.close()
+
+
+def test_fused_two_levels_grid_threshold(monkeypatch):
+    """By default an apply fuses from 4 blocks per SM (nrhs n_0 >= 4 x SMs):
+    on (76, 64, 64) eight right-hand sides fuse and one does not, and both
+    results match the oracle."""
+    monkeypatch.delenv("BTMV_FUSE_MIN_BLOCKS", raising=False)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    n0 = -(-4 * nsm // 8)
+    n, r = (n0, 64, 64), 8
+    t_orth, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    x = W.random_vector(n, 3, seed=99, nrhs=r)
+    ref = OE.embed_matvec(W.orthant_to_full(t_orth, par), round_input(x, 0))
+    plan = bt.Plan(n, 3, 0, max_rhs=r, flags=bt.BTMV_FLAG_FUSED_LEVELS | bt.BTMV_FLAG_PROFILE)
+    try:
+        plan.set_kernel(t_orth, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+        assert plan.info["launches_per_apply"] == 4
+        xd = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+        yd = torch.zeros_like(xd)
+        bt.btmv_profile_read(plan.handle)
+        plan.apply(xd, yd, r)
+        prof = bt.btmv_profile_read(plan.handle)
+        assert prof["fused_levels"][1] == 2 and prof["leaf"][1] == 0
+        assert rel(yd.cpu().numpy().astype(np.complex128), ref) <= 1e-5
+        y1 = torch.zeros_like(xd[:1])
+        plan.apply(xd[:1], y1, 1)
+        prof = bt.btmv_profile_read(plan.handle)
+        assert prof["fused_levels"][1] == 0 and prof["leaf"][1] == 2
+        assert rel(y1.cpu().numpy().astype(np.complex128), ref[:1]) <= 1e-5
     finally:
         plan.close()
