@@ -355,8 +355,8 @@ def measure_single(args, cfg, ws, rank, local):
 
     # dominant kernel and its roofline (algorithmic bytes per launch / event time)
     sym_b = info["symbol_bytes"]
-    pb = A.split_pass_bytes(n, c, 1, esz, sym_b)
-    kind_bytes = {"fwd_split": pb["fwd_split"], "leaf": pb["leaf"], "merge": pb["bwd_merge"]}
+    pb = A.apply_kind_bytes(n, c, 1, esz, sym_b, one_kernel=len(n) == 2 and info["launches_per_apply"] == 1)
+    kind_bytes = {k: v for k, v in pb.items() if k not in ("total", "V")}
     dom = max((k for k in kind_bytes if prof[k][1] > 0), key=lambda k: prof[k][0])
     per_apply_launches = prof[dom][1] / sampled
     bytes_per_launch = kind_bytes[dom] / per_apply_launches
@@ -518,8 +518,9 @@ def compact_single(args, workload, steps):
     ms = e0.elapsed_time(e1) / steps
     prof = bt.btmv_profile_read(plan.handle)
     sampled = (steps + 4) // 5
-    pb = A.split_pass_bytes(n, c, 1, esz, info["symbol_bytes"])
-    kind_bytes = {"fwd_split": pb["fwd_split"], "leaf": pb["leaf"], "merge": pb["bwd_merge"]}
+    pb = A.apply_kind_bytes(n, c, 1, esz, info["symbol_bytes"],
+                            one_kernel=len(n) == 2 and info["launches_per_apply"] == 1)
+    kind_bytes = {k: v for k, v in pb.items() if k not in ("total", "V")}
     peak = float(measured_peaks()[0]["hbm_gbs"])
     kernels = {}
     for k, b in kind_bytes.items():

@@ -116,6 +116,21 @@ def fused_pass_bytes(n, c: int, nrhs: int, elem_bytes: int, sym_bytes: int) -> d
             "total": 6 * V + fused, "V": V}
 
 
+def apply_kind_bytes(n, c: int, nrhs: int, elem_bytes: int, sym_bytes: int, one_kernel: bool = False) -> dict:
+    """Algorithmic bytes per profile kind of one split apply: the split
+    schedule's kinds (split_pass_bytes), or, for a d = 2 apply run as one
+    cluster kernel (one_kernel), that kernel's x read, y written and symbol
+    read once: 2 V + symbol under the kind "fused_levels"."""
+    if one_kernel:
+        if len(n) != 2:
+            raise ValueError("the one-kernel apply is d = 2")
+        V = vector_bytes(n, c, nrhs, elem_bytes)
+        return {"fused_levels": 2 * V + sym_bytes, "total": 2 * V + sym_bytes, "V": V}
+    pb = split_pass_bytes(n, c, nrhs, elem_bytes, sym_bytes)
+    return {"fwd_split": pb["fwd_split"], "leaf": pb["leaf"], "merge": pb["bwd_merge"],
+            "total": pb["total"], "V": pb["V"]}
+
+
 def full_pass_bytes(n, c: int, nrhs: int, elem_bytes: int, sym_bytes: int) -> dict:
     """Algorithmic bytes of the plain full embedding with the library's own
     kernels: the first pass reads x (V) and writes the zero-padded,

@@ -857,8 +857,25 @@ static btmv_status run_steps(btmv_plan p, const std::vector<Step>& steps, int nr
   return BTMV_OK;
 }
 
+// d = 2, c = 1, 64 x 64: the three kernels of the split apply (dim-0 split,
+// leaf, dim-0 merge) as one launch of a thread-block cluster per right-hand
+// side (small2d.cu).  BTMV_SMALL2D=0 in the environment, or
+// BTMV_FLAG_GENERIC, keeps the three kernels (comparisons).
+bool btmv::use_small2d(btmv_plan p) {
+  if (p->algo != BTMV_ALGO_SPLIT || (p->flags & BTMV_FLAG_GENERIC)) return false;
+  const char* v = getenv("BTMV_SMALL2D");
+  if (v && v[0] == '0') return false;
+  return small2d_supported(p->d, p->c, p->n, p->symdev) && p->fft_apply[0].N == 64 && p->fft_apply[1].N == 64;
+}
+
 template <class T>
 static btmv_status split_apply(btmv_plan p, const void* x, void* y, int nrhs, cudaStream_t st) {
+  if (use_small2d(p)) {
+    ProfScope ps(p, BTMV_K_FUSED_LEVELS, st);
+    const cudaError_t e = launch_small2d(x, y, nrhs, sizeof(T) == sizeof(double2), p->fft_apply[0], p->symdev, st);
+    if (e != cudaSuccess) return fail(BTMV_E_CUDA, "small two-level apply: %s", cudaGetErrorString(e));
+    return BTMV_OK;
+  }
   std::vector<Step> steps;
   const bool fuse = fuse_this_apply(p, nrhs, y);
   if (!p->side) {
@@ -1104,7 +1121,7 @@ extern "C" const char* btmv_last_error(void) { return g_err.c_str(); }
 static int launches_per_apply(btmv_plan p) {
   const int d = p->d;
   if (p->algo == BTMV_ALGO_SPLIT) {
-    if (d == 1) return 1;
+    if (d == 1 || use_small2d(p)) return 1;
     int n = 0;
     if (two_level_fusable(p) && (long long)p->max_rhs * p->n[0] >= fuse_min_blocks(p)) {
       // forward + merge per node of levels 0..d-3, one fused launch per level-(d-2) node

@@ -132,6 +132,13 @@ bool fuse_this_apply(btmv_plan p, int nrhs, const void* y);
 bool fuse2_supported(int d, int c, const int* n, size_t esz, const SymDev& S);
 cudaError_t launch_fuse2(float2* node, float2* scratch, int prefix0, int n0, int nrhs, const FftDev& f1,
                          const FftDev& f2, const SymDev& sym, cudaStream_t st);
+// The whole apply of a d = 2, c = 1, 64 x 64 split plan as one cluster
+// kernel (small2d.cu); dbl: complex128.
+bool small2d_supported(int d, int c, const int* n, const SymDev& S);
+cudaError_t launch_small2d(const void* x, void* y, int nrhs, bool dbl, const FftDev& f, const SymDev& sym,
+                           cudaStream_t st);
+// The plan's applies take launch_small2d.
+bool use_small2d(btmv_plan p);
 // Arguments of a split pass step; TL = 0 picks the default tile.
 PassArgs split_pass_args(btmv_plan p, const Step& s, int nrhs, size_t esz, int TL);
 // Arguments of a leaf step; Lt, rq = 0 pick the defaults.

@@ -65,3 +65,16 @@ def test_fused_pass_bytes_drop_the_inner_levels():
     assert fused["fwd_split"] + fused["bwd_merge"] == 6 * V
     with pytest.raises(ValueError):
         A.fused_pass_bytes((8, 8), 1, 1, 8, 0)
+
+
+def test_apply_kind_bytes_one_kernel_and_split():
+    """Per-kind bytes: the split kinds sum to the split total; the d = 2 apply
+    as one cluster kernel moves x and y once plus the symbol."""
+    n, S = (64, 64), 777
+    V = 64 * 64 * 16
+    one = A.apply_kind_bytes(n, 1, 1, 16, S, one_kernel=True)
+    assert one["fused_levels"] == one["total"] == 2 * V + S
+    sp = A.apply_kind_bytes(n, 1, 1, 16, S)
+    assert sp["fwd_split"] + sp["leaf"] + sp["merge"] == sp["total"] == 10 * V + S
+    with pytest.raises(ValueError):
+        A.apply_kind_bytes((8, 8, 8), 1, 1, 8, 0, one_kernel=True)

@@ -652,3 +652,54 @@ def test_fused_two_levels_grid_threshold(monkeypatch):
         assert rel(y1.cpu().numpy().astype(np.complex128), ref[:1]) <= 1e-5
     finally:
         plan.close()
+
+
+SMALL2D_CASES = [("random", 0, 1), ("random", 1, 3), ("green", 0, 2), ("green", 1, 1), ("skew", 1, 2),
+                 ("mixed", 0, 1), ("mixed", 1, 2)]
+
+
+def _small2d_instance(kind, n):
+    if kind == "random":
+        return W.random_generator(n, 1, seed=301), None, 0
+    if kind == "green":
+        t, par = W.green_scalar_orthant(n, kh=W.KH_GREEN)
+        return t, par, bt.BTMV_SYM_PARITY
+    if kind == "skew":
+        t, par = W.skew_orthant(n, seed=302, c=1)
+        return t, par, bt.BTMV_SYM_PARITY
+    par = np.array([[[1, -1]]], dtype=np.int8)
+    return W.random_parity_orthant(n, 1, seed=303, parity=par, block_sym=False), par, bt.BTMV_SYM_PARITY
+
+
+@pytest.mark.parametrize("kind,precision,nrhs", SMALL2D_CASES)
+def test_small_two_level_cluster_apply(kind, precision, nrhs, monkeypatch):
+    """d = 2, c = 1, 64 x 64: the whole split apply as one launch of a
+    thread-block cluster per right-hand side (columns, leaf rows and columns
+    again exchanged through distributed shared memory) against the FP64
+    oracle and the three-kernel schedule, on the full store and on the
+    compressed store with even, odd and mixed parities."""
+    n = (64, 64)
+    t, par, sym = _small2d_instance(kind, n)
+    x = W.random_vector(n, 1, seed=304, nrhs=nrhs)
+    full = W.orthant_to_full(t, par) if par is not None else t
+    ref = OE.embed_matvec(full, round_input(x, precision))
+    monkeypatch.setenv("BTMV_SMALL2D", "0")
+    y0 = run_btmv(t, x, n, 1, precision, 0, sym, par)
+    monkeypatch.delenv("BTMV_SMALL2D")
+    y1 = run_btmv(t, x, n, 1, precision, 0, sym, par)
+    assert rel(y1, ref) <= TOL[precision]
+    assert rel(y1, y0) <= (1e-6 if precision == 0 else 1e-13)
+    plan = bt.Plan(n, 1, precision, max_rhs=nrhs, flags=bt.BTMV_FLAG_PROFILE)
+    try:
+        plan.set_kernel(t, sym, par)
+        assert plan.info["launches_per_apply"] == 1
+        dt = np.complex64 if precision == 0 else np.complex128
+        xd = torch.from_numpy(np.ascontiguousarray(x.astype(dt))).cuda()
+        yd = torch.zeros_like(xd)
+        bt.btmv_profile_read(plan.handle)
+        plan.apply(xd, yd, nrhs)
+        prof = bt.btmv_profile_read(plan.handle)
+        assert prof["fused_levels"][1] == 1 and prof["leaf"][1] == 0
+        assert rel(yd.cpu().numpy().astype(np.complex128), ref) <= TOL[precision]
+    finally:
+        plan.close()
