@@ -90,6 +90,7 @@ KERNEL_SOURCES = {
     "fwd_split": ["fast_pass.cu", "fast_pass_tma.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
     "merge": ["fast_pass.cu", "fast_pass_tma.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
     "fused2": ["fused2.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
+    "small2d": ["small2d.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
 }
 
 
@@ -466,7 +467,8 @@ def measure_single(args, cfg, ws, rank, local):
                    "parallelism": f"{ws} independent instance(s), one per GPU"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
-                     "traffic": ncu_traffic(dom, args.workload),
+                     "traffic": ncu_traffic("small2d" if dom == "fused_levels" and len(n) == 2 else dom,
+                                            args.workload),
                      "algorithmic_bytes_per_launch": bytes_per_launch},
         "whole_step_algo_GBps": whole_GBps,
         "kernels": kernels,
