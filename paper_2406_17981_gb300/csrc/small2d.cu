@@ -22,7 +22,9 @@
 // every CTA of the cluster runs before any remote store); no CTA touches
 // another's shared memory after the last one.  A line of 64 points is held
 // by 8 threads, 8 points each, and transformed in two radix-8 stages that
-// exchange through a per-group buffer, as in the fused d = 3 kernel.
+// exchange through a per-group buffer, as in the fused d = 3 kernel; the
+// leaf runs the two halves b1 of a row in two groups (twice the threads of
+// the column phases, where half of the warps idle).
 #include <cooperative_groups.h>
 
 #include <cstdint>
@@ -77,10 +79,11 @@ struct Small2dArgs {
 template <class T, int K>
 struct Small2dCfg {
   static constexpr int R = s2::N / K;          // columns (rows) per CTA
-  static constexpr int G = 2 * R;              // 8-thread groups: R lines x 2 children
+  static constexpr int L = 2 * R;              // lines per phase: R columns (rows) x 2 children
+  static constexpr int G = 2 * L;              // 8-thread groups: the leaf runs its two halves b1 apart
   static constexpr int THREADS = 8 * G;
-  // rows[2][R][N] | cols[2][R][N] | exchange[G][N] | twiddles[8][9] | phase[N]
-  static constexpr size_t SMEM = (size_t)(4 * R * s2::N + G * s2::N + 72 + s2::N) * sizeof(T);
+  // rows[L][N] | cols[L][N] | odd[L][N] | exchange[G][N] | twiddles[8][9] | phase[N]
+  static constexpr size_t SMEM = (size_t)(3 * L * s2::N + G * s2::N + 72 + s2::N) * sizeof(T);
 };
 
 template <class T, int K>
@@ -89,9 +92,11 @@ __global__ void __launch_bounds__(Small2dCfg<T, K>::THREADS) k_small2d(const Sma
   typedef Small2dCfg<T, K> CF;
   constexpr int R = CF::R;
   extern __shared__ __align__(16) unsigned char s2mem[];
+  constexpr int L = CF::L;
   T* const rows = (T*)s2mem;                       // [2][R][N]: rows of both children owned here
-  T* const cols = rows + 2 * R * N;                // [2][R][N]: columns of both children owned here
-  T* const xbuf = cols + 2 * R * N;                // [G][N]
+  T* const cols = rows + L * N;                    // [2][R][N]: columns of both children owned here
+  T* const odd = cols + L * N;                     // [2][R][N]: the leaf's odd halves
+  T* const xbuf = odd + L * N;                     // [G][N]
   T* const twt = xbuf + CF::G * N;                 // [8][9]
   T* const phs = twt + 72;                         // [N]
   cgx::cluster_group cluster = cgx::this_cluster();
@@ -109,8 +114,9 @@ __global__ void __launch_bounds__(Small2dCfg<T, K>::THREADS) k_small2d(const Sma
   __syncthreads();
   cluster.sync();                                  // every CTA of the cluster is running
 
-  // 1: column i1 of child b0, forward along dim 0, each value sent to the owner of its row
-  {
+  // 1: column i1 of child b0, forward along dim 0, each value sent to the owner
+  // of its row (groups g < L; the others idle as whole warps)
+  if (g < L) {
     const int j = g % R, b0 = g / R, i1 = R * k + j;
     T v[8];
 #pragma unroll
@@ -127,68 +133,70 @@ __global__ void __launch_bounds__(Small2dCfg<T, K>::THREADS) k_small2d(const Sma
   }
   cluster.sync();
 
-  // 2: the leaf on row f0 of child b0 (dim-0 frequency 2 f0 + b0), result
-  // values sent to the owners of their columns
+  // 2: the leaf on row f0 of child b0 (dim-0 frequency 2 f0 + b0), half b1
+  // in group b1 L + line; the even half adds the odd half's conj(P1) term and
+  // sends each result value to the owner of its column
   {
-    const int r = g % R, b0 = g / R, f0 = R * k + r;
-    const T* const row = rows + (b0 * R + r) * N;
+    const int b1 = g / L, line = g % L, r = line % R, b0 = line / R, f0 = R * k + r;
+    const T* const row = rows + line * N;
     const SymDev& S = a.sym;
     int fp0 = 2 * f0 + b0, foldp = 0;
     if (S.compressed && fp0 > S.n[0]) { fp0 = 2 * S.n[0] - fp0; foldp = 1; }
-    const long long lin = fp0 >> 1;
-    T r0[8], v[8];
-#pragma unroll
-    for (int b1 = 0; b1 < 2; ++b1) {
-      const int c = (b0 << 1) | b1;
-      const T* __restrict__ rw = (const T*)S.data + S.cls_off[c] + lin * S.J[c][1];
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const T e = row[t + 8 * m];
-        v[m] = b1 ? cmul(e, phs[t + 8 * m]) : e;
-      }
-      fft64<false>(v, t, xv, tw);
-      // frequency f = 2 l + b1, l = t + 8 m: full store at l; compressed
-      // store at l for l < N/2, else at N - b1 - l with the fold's sign
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int l = t + 8 * m;
-        const bool hi = S.compressed && l >= N / 2;
-        T s = __ldg(rw + (hi ? N - b1 - l : l));
-        if (__popc(S.oddmask[0] & (hi ? (foldp | 2) : foldp)) & 1) { s.x = -s.x; s.y = -s.y; }
-        v[m] = cmul(s, v[m]);
-      }
-      fft64<true>(v, t, xv, tw);
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        if (b1 == 0) r0[m] = v[m];
-        else v[m] = cadd(r0[m], cmulc(v[m], phs[t + 8 * m]));
-      }
-    }
+    const int c = (b0 << 1) | b1;
+    const T* __restrict__ rw = (const T*)S.data + S.cls_off[c] + (long long)(fp0 >> 1) * S.J[c][1];
+    T v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-      const int i1 = t + 8 * m;
-      *cluster.map_shared_rank(cols + (b0 * R + i1 % R) * N + f0, i1 / R) = v[m];
+      const T e = row[t + 8 * m];
+      v[m] = b1 ? cmul(e, phs[t + 8 * m]) : e;
+    }
+    fft64<false>(v, t, xv, tw);
+    // frequency f = 2 l + b1, l = t + 8 m: full store at l; compressed
+    // store at l for l < N/2, else at N - b1 - l with the fold's sign
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int l = t + 8 * m;
+      const bool hi = S.compressed && l >= N / 2;
+      T s = __ldg(rw + (hi ? N - b1 - l : l));
+      if (__popc(S.oddmask[0] & (hi ? (foldp | 2) : foldp)) & 1) { s.x = -s.x; s.y = -s.y; }
+      v[m] = cmul(s, v[m]);
+    }
+    fft64<true>(v, t, xv, tw);
+    if (b1 == 1) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) odd[line * N + t + 8 * m] = cmulc(v[m], phs[t + 8 * m]);
+    }
+    __syncthreads();
+    if (b1 == 0) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int i1 = t + 8 * m;
+        *cluster.map_shared_rank(cols + (b0 * R + i1 % R) * N + f0, i1 / R) = cadd(v[m], odd[line * N + i1]);
+      }
     }
   }
   cluster.sync();                                  // no remote access after this
 
   // 3: column i1 of both children inverse along dim 0, y = z_0 + conj(P0) z_1
+  // (groups g < L)
   {
     const int j = g % R, b0 = g / R, i1 = R * k + j;
     T* const col = cols + (b0 * R + j) * N;
     T v[8];
+    if (g < L) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = col[t + 8 * m];
-    fft64<true>(v, t, xv, tw);
-    if (b0 == 1) {
+      for (int m = 0; m < 8; ++m) v[m] = col[t + 8 * m];
+      fft64<true>(v, t, xv, tw);
+      if (b0 == 1) {
 #pragma unroll
-      for (int m = 0; m < 8; ++m) col[t + 8 * m] = cmulc(v[m], phs[t + 8 * m]);
+        for (int m = 0; m < 8; ++m) col[t + 8 * m] = cmulc(v[m], phs[t + 8 * m]);
+      }
     }
     __syncthreads();
-    if (b0 == 0) {
-      const T* const odd = cols + (R + j) * N;
+    if (g < L && b0 == 0) {
+      const T* const z1 = cols + (R + j) * N;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) y[(long long)(t + 8 * m) * N + i1] = cadd(v[m], odd[t + 8 * m]);
+      for (int m = 0; m < 8; ++m) y[(long long)(t + 8 * m) * N + i1] = cadd(v[m], z1[t + 8 * m]);
     }
   }
 }
