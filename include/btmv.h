@@ -198,13 +198,18 @@ BTMV_API btmv_status btmv_set_kernel(btmv_plan p, const double* t, uint32_t sym_
 /*
  * btmv_apply -- y = T x for nrhs right-hand sides.
  *   x, y      [nrhs][c][n_1]..[n_d] complex (plan precision); device or host
- *             pointers; must not overlap.  x is read only, y is overwritten.
+ *             pointers, 16-byte aligned; must not overlap.  x is read only,
+ *             y is overwritten.
  *   nrhs      0 <= nrhs <= max_rhs (0 is a no-op).
  *   stream    work is enqueued on it; with host pointers the call copies
  *             through plan-owned device buffers and synchronises the stream.
  * SPLIT: depth-first traversal of Algorithm 1 -- forward split passes along
  * levels 1..d-1, a fused leaf pass along level d (both halves, symbol
- * multiply, merge), merge passes back up; peak (d+1) vectors.
+ * multiply, merge), merge passes back up; peak (d+1) vectors.  d = 2, c = 1,
+ * 64 x 64 plans run the whole traversal as one launch of a 16-CTA cluster
+ * per right-hand side (BTMV_SMALL2D=0 in the environment, or
+ * BTMV_FLAG_GENERIC, keeps the three kernels); BTMV_FLAG_FUSED_LEVELS fuses
+ * the last two levels of d = 3 plans it supports.
  * Errors: BTMV_E_ARG, BTMV_E_STATE (no generator set), BTMV_E_CUDA,
  * BTMV_E_TIMEOUT (a bounded wait of a TMA-staged pass expired in an earlier
  * apply on this plan; reported once, by the next apply).
