@@ -87,3 +87,35 @@ def test_adjoint_identity_at_benchmark_size(name):
     rhs = np.vdot(thz, x.astype(np.complex128))          # (T^H z)^H x
     scale = np.linalg.norm(tx) * np.linalg.norm(z)
     assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+def test_fused_levels_bench_size_sampled_direct_sum():
+    """The fused last two levels (BTMV_FLAG_FUSED_LEVELS) at the size
+    bench.py times them, 512 x 64 x 64 c=3 Green with 8 right-hand sides:
+    every right-hand side against the direct sum at the grid's corners and
+    six sampled points, and the whole output against the unfused schedule."""
+    import bench
+    from tests.gpu_util import sample_points
+    n, r = (512, 64, 64), 8
+    assert (bench.FUSED_N, bench.FUSED_RHS) == (n, r)
+    t, par = W.green_dyadic_orthant(n, kh=W.KH_GREEN)
+    x = W.random_vector(n, 3, seed=37, nrhs=r).astype(np.complex64)
+    xd = torch.from_numpy(x).cuda()
+    ys = []
+    for fl in (bt.BTMV_FLAG_FUSED_LEVELS | bt.BTMV_FLAG_PROFILE, 0):
+        plan = bt.Plan(n, 3, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=r, flags=fl)
+        plan.set_kernel(t, 3, par)
+        yd = torch.zeros_like(xd)
+        if fl:
+            bt.btmv_profile_read(plan.handle)
+        plan.apply(xd, yd, r)
+        if fl:
+            assert bt.btmv_profile_read(plan.handle)["fused_levels"][1] == 2
+        ys.append(yd.cpu().numpy().astype(np.complex128))
+        plan.close()
+    yf, yu = ys
+    assert rel(yf, yu) <= 1e-6
+    pts = sample_points(n, 6, seed=43)
+    vals = OT.direct_points(W.orthant_to_full(t, par), x.astype(np.complex128), pts)   # [npts][r][c]
+    got = np.stack([yf[(slice(None), slice(None)) + p] for p in pts])
+    assert rel(got, vals) <= 1e-5
