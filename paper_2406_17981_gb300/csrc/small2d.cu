@@ -230,11 +230,11 @@ static cudaError_t small2d_k(const Small2dArgs& a, int nrhs, cudaStream_t st) {
 }
 
 // Clusters of 16 CTAs where the device schedules them (a non-portable
-// size), else of 8.  Errors: cudaErrorInvalidValue for nrhs outside
-// [1, 65535].
+// size), else of 8; right-hand sides on the grid's y dimension, at most
+// 65535 per launch (more are launched in chunks).
 template <class T>
 static cudaError_t small2d_t(const Small2dArgs& a, int nrhs, cudaStream_t st) {
-  if (nrhs < 1 || nrhs > 65535) return cudaErrorInvalidValue;
+  if (nrhs < 1) return cudaErrorInvalidValue;
   static int k16[64] = {0};                        // per device: 0 unknown, 1 yes, 2 no
   int dev = 0;
   cudaGetDevice(&dev);
@@ -258,7 +258,16 @@ static cudaError_t small2d_t(const Small2dArgs& a, int nrhs, cudaStream_t st) {
     ok = (attr && cudaOccupancyMaxActiveClusters(&maxc, k_small2d<T, 16>, &cfg) == cudaSuccess && maxc > 0) ? 1 : 2;
     cudaGetLastError();
   }
-  return ok == 1 ? small2d_k<T, 16>(a, nrhs, st) : small2d_k<T, 8>(a, nrhs, st);
+  constexpr int YMAX = 65535;
+  for (int q0 = 0; q0 < nrhs; q0 += YMAX) {
+    Small2dArgs c = a;
+    c.x = (const T*)a.x + (size_t)q0 * s2::N * s2::N;
+    c.y = (T*)a.y + (size_t)q0 * s2::N * s2::N;
+    const int nq = nrhs - q0 < YMAX ? nrhs - q0 : YMAX;
+    const cudaError_t e = ok == 1 ? small2d_k<T, 16>(c, nq, st) : small2d_k<T, 8>(c, nq, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_small2d(const void* x, void* y, int nrhs, bool dbl, const FftDev& f, const SymDev& sym,

@@ -703,3 +703,34 @@ def test_small_two_level_cluster_apply(kind, precision, nrhs, monkeypatch):
         assert rel(yd.cpu().numpy().astype(np.complex128), ref) <= TOL[precision]
     finally:
         plan.close()
+
+
+def test_small_two_level_more_rhs_than_one_grid_dimension(monkeypatch):
+    """More than 65535 right-hand sides (the grid's y limit) run the
+    one-launch d = 2 apply in chunks: the right-hand sides on both sides of
+    each chunk boundary and the last one against the FP64 oracle, sampled
+    right-hand sides against the three-kernel schedule."""
+    n, r = (64, 64), 65535 + 4
+    t = W.random_generator(n, 1, seed=305)
+    g = torch.Generator(device="cuda").manual_seed(306)
+    xd = torch.randn((r, 1) + n, dtype=torch.complex64, device="cuda", generator=g)
+    ys = {}
+    for env in ("1", "0"):
+        monkeypatch.setenv("BTMV_SMALL2D", env)
+        plan = bt.Plan(n, 1, 0, max_rhs=r)
+        try:
+            plan.set_kernel(t)
+            yd = torch.zeros_like(xd)
+            plan.apply(xd, yd, r)
+            torch.cuda.synchronize()
+            ys[env] = yd
+        finally:
+            plan.close()
+    for q in (0, 65534, 65535, r - 1):
+        xq = xd[q:q + 1].cpu().numpy().astype(np.complex128)
+        ref = OE.embed_matvec(t, xq)
+        assert rel(ys["1"][q:q + 1].cpu().numpy().astype(np.complex128), ref) <= 1e-5
+    idx = torch.arange(0, r, 997, device="cuda")
+    a = ys["1"][idx].cpu().numpy().astype(np.complex128)
+    b = ys["0"][idx].cpu().numpy().astype(np.complex128)
+    assert rel(a, b) <= 1e-6
