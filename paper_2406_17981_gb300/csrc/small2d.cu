@@ -28,6 +28,7 @@
 #include <cooperative_groups.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 
 #include "../../include/btmv.h"
@@ -230,7 +231,8 @@ static cudaError_t small2d_k(const Small2dArgs& a, int nrhs, cudaStream_t st) {
 }
 
 // Clusters of 16 CTAs where the device schedules them (a non-portable
-// size), else of 8; right-hand sides on the grid's y dimension, at most
+// size), else of 8 (BTMV_SMALL2D_CLUSTER=8 in the environment forces 8, to
+// exercise that form); right-hand sides on the grid's y dimension, at most
 // 65535 per launch (more are launched in chunks).
 template <class T>
 static cudaError_t small2d_t(const Small2dArgs& a, int nrhs, cudaStream_t st) {
@@ -238,7 +240,10 @@ static cudaError_t small2d_t(const Small2dArgs& a, int nrhs, cudaStream_t st) {
   static int k16[64] = {0};                        // per device: 0 unknown, 1 yes, 2 no
   int dev = 0;
   cudaGetDevice(&dev);
-  int& ok = k16[dev & 63];
+  int& ok16 = k16[dev & 63];
+  const char* force = getenv("BTMV_SMALL2D_CLUSTER");
+  int forced = (force && force[0] == '8') ? 2 : 0;
+  int& ok = forced ? forced : ok16;
   if (ok == 0) {
     typedef Small2dCfg<T, 16> CF;
     int maxc = 0;

@@ -672,12 +672,16 @@ def _small2d_instance(kind, n):
 
 
 @pytest.mark.parametrize("kind,precision,nrhs", SMALL2D_CASES)
-def test_small_two_level_cluster_apply(kind, precision, nrhs, monkeypatch):
+@pytest.mark.parametrize("cluster", ["16", "8"])
+def test_small_two_level_cluster_apply(kind, precision, nrhs, cluster, monkeypatch):
     """d = 2, c = 1, 64 x 64: the whole split apply as one launch of a
     thread-block cluster per right-hand side (columns, leaf rows and columns
     again exchanged through distributed shared memory) against the FP64
     oracle and the three-kernel schedule, on the full store and on the
-    compressed store with even, odd and mixed parities."""
+    compressed store with even, odd and mixed parities; clusters of 16 CTAs
+    (taken on GB300) and of 8 (the form for devices that refuse 16)."""
+    if cluster == "8":
+        monkeypatch.setenv("BTMV_SMALL2D_CLUSTER", "8")
     n = (64, 64)
     t, par, sym = _small2d_instance(kind, n)
     x = W.random_vector(n, 1, seed=304, nrhs=nrhs)
