@@ -112,16 +112,18 @@ enum {
                                       passes of one overlap the leaves of the
                                       other; costs d-2 more workspace vectors
                                       (peak d+1 -> 2d-1 vectors)              */
-  BTMV_FLAG_FUSED_LEVELS = 1u << 5 /* split, d = 3, c = 3, complex64, block-
-                                      symmetric compressed store, n_1 = n_2 =
-                                      64: the last two levels of Algorithm 1
-                                      (the dim-1 split, the leaf, the dim-1
-                                      merge) run as one kernel per level-1
-                                      node, its n_1 x n_2 slabs held in shared
-                                      memory (Sec. II.B); other plans ignore
-                                      the flag.  An apply fuses when its grid
-                                      has at least 4 blocks per SM (nrhs n_0 >=
-                                      4 x SMs; BTMV_FUSE_MIN_BLOCKS=k in the
+  BTMV_FLAG_FUSED_LEVELS = 1u << 5 /* split, d >= 3, c = 3, complex64,
+                                      block-symmetric compressed store,
+                                      n_{d-1} = n_d = 64 (1-based levels): the
+                                      last two levels of Algorithm 1 (the
+                                      level d-1 split, the leaf, the level
+                                      d-1 merge) run as one kernel per level
+                                      d-2 node, its n_{d-1} x n_d slabs held
+                                      in shared memory (Sec. II.B); other
+                                      plans ignore the flag.  An apply fuses
+                                      when its grid has at least 4 blocks per
+                                      SM (nrhs n_1 .. n_{d-2} >= 4 x SMs;
+                                      BTMV_FUSE_MIN_BLOCKS=k in the
                                       environment sets k), else it runs
                                       unfused; plan info counts launches for
                                       max_rhs                                 */

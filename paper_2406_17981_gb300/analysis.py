@@ -101,19 +101,22 @@ def split_pass_bytes(n, c: int, nrhs: int, elem_bytes: int, sym_bytes: int) -> d
 
 
 def fused_pass_bytes(n, c: int, nrhs: int, elem_bytes: int, sym_bytes: int) -> dict:
-    """Algorithmic bytes of a d = 3 split apply with the last two levels
-    fused (BTMV_FLAG_FUSED_LEVELS): the dim-0 split reads x and writes both
-    level-1 nodes (3V), each fused launch reads its node and writes it back
-    (2V; the levels below it stay on chip), the symbol is read once, and the
-    dim-0 merge reads both nodes and writes y (3V).  The fused kernel's
-    scratch vector (the even half of the dim-1 merge parked off chip) is an
-    implementation cost, not counted here."""
-    if len(n) != 3:
-        raise ValueError("the fused schedule is d = 3")
+    """Algorithmic bytes of a split apply (d >= 3) with the last two levels
+    fused (BTMV_FLAG_FUSED_LEVELS): the forward splits and merges of levels
+    1..d-2 as in split_pass_bytes (each 3V per node), each of the 2^(d-2)
+    fused launches reading its level-(d-2) node and writing it back (2V; the
+    levels below it stay on chip), and the symbol read once.  The fused
+    kernel's scratch vector (the even half of the column-dim merge parked off
+    chip) is an implementation cost, not counted here.  d = 3: 10 V + symbol
+    against 26 V + symbol unfused."""
+    d = len(n)
+    if d < 3:
+        raise ValueError("the fused schedule needs d >= 3")
     V = vector_bytes(n, c, nrhs, elem_bytes)
-    fused = 2 * 2 * V + sym_bytes
-    return {"fwd_split": 3 * V, "fused_levels": fused, "bwd_merge": 3 * V,
-            "total": 6 * V + fused, "V": V}
+    passes = sum(2 ** (m - 1) * 3 * V for m in range(1, d - 1))
+    fused = 2 ** (d - 2) * 2 * V + sym_bytes
+    return {"fwd_split": passes, "fused_levels": fused, "bwd_merge": passes,
+            "total": 2 * passes + fused, "V": V}
 
 
 def apply_kind_bytes(n, c: int, nrhs: int, elem_bytes: int, sym_bytes: int, one_kernel: bool = False) -> dict:

@@ -818,9 +818,16 @@ static long long fuse_min_blocks(btmv_plan p) {
   return 4ll * std::max(1, p->nsm);
 }
 
+// blocks of one fused launch: one per prefix index and right-hand side
+static long long fuse_blocks(btmv_plan p, int nrhs) {
+  long long b = nrhs;
+  for (int m = 0; m + 2 < p->d; ++m) b *= p->n[m];
+  return b;
+}
+
 bool btmv::fuse_this_apply(btmv_plan p, int nrhs, const void* y) {
   if (!two_level_fusable(p) || ((uintptr_t)y & 15)) return false;
-  return (long long)nrhs * p->n[0] >= fuse_min_blocks(p);
+  return fuse_blocks(p, nrhs) >= fuse_min_blocks(p);
 }
 
 void btmv::split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& out, bool fuse) {
@@ -841,7 +848,7 @@ void btmv::split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& o
 static btmv_status fused_levels(btmv_plan p, const Step& s, int nrhs, cudaStream_t st) {
   ProfScope ps(p, BTMV_K_FUSED_LEVELS, st);
   const int m = s.dim;
-  cudaError_t e = launch_fuse2((float2*)s.out0, (float2*)s.out1, s.nodes[0].prefix, p->n[0], nrhs,
+  cudaError_t e = launch_fuse2((float2*)s.out0, (float2*)s.out1, s.nodes[0].prefix, p->d, p->n, nrhs,
                                p->fft_apply[m], p->fft_apply[m + 1], p->symdev, st);
   if (e != cudaSuccess) return fail(BTMV_E_CUDA, "fused levels: %s", cudaGetErrorString(e));
   return BTMV_OK;
@@ -1123,7 +1130,7 @@ static int launches_per_apply(btmv_plan p) {
   if (p->algo == BTMV_ALGO_SPLIT) {
     if (d == 1 || use_small2d(p)) return 1;
     int n = 0;
-    if (two_level_fusable(p) && (long long)p->max_rhs * p->n[0] >= fuse_min_blocks(p)) {
+    if (two_level_fusable(p) && fuse_blocks(p, p->max_rhs) >= fuse_min_blocks(p)) {
       // forward + merge per node of levels 0..d-3, one fused launch per level-(d-2) node
       for (int m = 0; m < d - 2; ++m) n += 2 * (1 << m);
       return n + (1 << (d - 2));

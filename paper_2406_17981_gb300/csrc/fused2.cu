@@ -1,25 +1,29 @@
 // Two-level fusion: the last two levels of Algorithm 1 for one node in one
 // kernel, with the node's slab held on chip.
 //
-// At d = 3 a level-1 node v (transformed along dim 0, parity prefix b0) is, in
-// the unfused schedule, split along dim 1 into two children (two more
-// vectors of HBM traffic each way), each child's leaf runs along dim 2, and
-// the children are merged back along dim 1 (Sec. II.B, Algorithm 1).  The
-// subtree below v acts on every dim-0 index i0 of v independently, so one
-// block takes the slab v[q][:][i0][:][:] (3 components x N1 x N2 points) into
-// shared memory and runs, for both halves b1 of dim 1:
+// A level-(d-2) node v (transformed along the prefix dims 0..d-3, parity
+// bits b_0..b_{d-3}) is, in the unfused schedule, split along dim d-2 into
+// two children (two more vectors of HBM traffic each way), each child's leaf
+// runs along dim d-1, and the children are merged back along dim d-2
+// (Sec. II.B, Algorithm 1).  The subtree below v acts on every prefix index
+// of v independently, so one block takes the slab of one prefix index (3
+// components x N1 x N2 points, N1 along dim d-2 = the columns, N2 along dim
+// d-1 = the rows) into shared memory and runs, for both halves b1 of the
+// column dim:
 //
-//   B  column transforms along dim 1 of P1^b1 v (the split, Sec. II.A),
-//   C  the leaf on each row: for both halves b2 of dim 2 the forward transform
-//      of P2^b2 row, the 3 x 3 symbol multiply of class (b0, b1, b2), the
-//      inverse transform, merged as y_e + conj(P2) y_o,
+//   B  column transforms of P1^b1 v (the split, Sec. II.A),
+//   C  the leaf on each row: for both halves b2 of the row dim the forward
+//      transform of P2^b2 row, the 3 x 3 symbol multiply of class
+//      (b_0..b_{d-3}, b1, b2), the inverse transform, merged as
+//      y_e + conj(P2) y_o,
 //   D  inverse column transforms,
-//   E  b1 = 0: the result (the even half of the merge along dim 1) is parked
-//      in a scratch vector; b1 = 1: v = parked + conj(P1) result (the merge).
+//   E  b1 = 0: the result (the even half of the merge along the column dim)
+//      is parked in a scratch vector; b1 = 1: v = parked + conj(P1) result
+//      (the merge).
 //
-// The slab stays on chip between the two levels: an apply moves about 16 V
-// (5 V per fused node: the node read twice, the scratch written and read,
-// the node written) instead of 26 V.
+// The slab stays on chip between the two levels: at d = 3 an apply moves
+// about 16 V (5 V per fused node: the node read twice, the scratch written
+// and read, the node written) instead of 26 V.
 //
 // Thread layout: 256 threads, 32 groups of 8, two blocks per SM (so that
 // one block's slab copies overlap the other's transforms); a 64-point line is
@@ -35,7 +39,7 @@
 // without bank conflicts and 16-byte pairs stay contiguous for the copies.
 //
 // Layout: c = 3 on the mirror-compressed block-symmetric store (stored
-// blocks 00 11 22 01 02 12), complex64, N1 = N2 = 64.
+// blocks 00 11 22 01 02 12), complex64, N1 = N2 = 64, d >= 3.
 #include <cstdint>
 #include <cstring>
 
@@ -115,8 +119,12 @@ __device__ __forceinline__ void chunk(int k, int& c, int& i1, int& i2) {
 struct FuseArgs {
   float2* node;              // the level-(d-2) node, updated in place
   float2* scratch;           // a vector the fused levels no longer need
-  int n0, nrhs, prefix0;     // dim-0 extent, right-hand sides, parity bit of dim 0
-  long long comp_stride;     // n0 * N1 * N2
+  int pd;                    // prefix dims 0..d-3 (d - 2 >= 1)
+  int ext[MAX_D];            // their extents
+  int prefix;                // the node's parity bits (bit m for prefix dim m)
+  int nrhs;
+  unsigned nslab;            // slabs per right-hand side: prod of the prefix extents
+  long long comp_stride;     // nslab * N1 * N2
   const float2* tw;          // exp(-2 pi i k / 64), k < 64
   const float2* ph;          // exp(-i pi k / 64), k < 64 (the split phase)
   SymDev sym;
@@ -130,10 +138,39 @@ __global__ void __launch_bounds__(fz::THREADS, 2) k_fuse2(const FuseArgs a) {
   float2* const twt = xb + GROUPS * N;             // [T][TWS] twiddles by thread
   const int g = threadIdx.x >> 3, t = threadIdx.x & 7;
   // blocks ordered right-hand side fastest: concurrent blocks share symbol rows
-  const unsigned i0 = blockIdx.x / (unsigned)a.nrhs;
-  const unsigned q = blockIdx.x - i0 * (unsigned)a.nrhs;
+  const unsigned sl = blockIdx.x / (unsigned)a.nrhs;   // slab (prefix index)
+  const unsigned q = blockIdx.x - sl * (unsigned)a.nrhs;
   const long long cs = a.comp_stride;
-  const long long slab_off = (long long)q * 3 * cs + (long long)i0 * N * N;
+  const long long slab_off = (long long)q * 3 * cs + (long long)sl * N * N;
+  const SymDev& S = a.sym;
+  // the slab's prefix frequencies 2 i_m + b_m (dims 0..pd-1, row-major
+  // slab index): their parity class bits, mirror folds and the prefix part
+  // of the symbol row index
+  int clspp = 0, foldpp = 0;
+  unsigned linp = 0;
+  {
+    int fpre[MAX_D - 2];
+    unsigned r = sl;
+#pragma unroll
+    for (int m = MAX_D - 3; m >= 0; --m)
+      if (m < a.pd) {
+        const unsigned e = (unsigned)a.ext[m], r2 = r / e;
+        fpre[m] = 2 * (int)(r - r2 * e) + ((a.prefix >> m) & 1);
+        r = r2;
+      }
+#pragma unroll
+    for (int m = 0; m < MAX_D - 2; ++m)
+      if (m < a.pd) {
+        clspp = (clspp << 1) | (fpre[m] & 1);
+        int fm = fpre[m];
+        if (fm > S.n[m]) { fm = 2 * S.n[m] - fm; foldpp |= 1 << m; }
+        fpre[m] = fm;
+      }
+    // strides of the prefix dims depend only on their own parity bits
+#pragma unroll
+    for (int m = 0; m < MAX_D - 2; ++m)
+      if (m < a.pd) linp = linp * (unsigned)S.J[clspp << 2][m] + (unsigned)(fpre[m] >> 1);
+  }
   if (threadIdx.x < N) {
     const int tt = threadIdx.x >> 3, r = threadIdx.x & 7;
     twt[tt * TWS + r] = __ldg(a.tw + r * tt);
@@ -143,7 +180,6 @@ __global__ void __launch_bounds__(fz::THREADS, 2) k_fuse2(const FuseArgs a) {
   // leaf rows rbase and rbase + 32: the two groups of a half-warp take rows 4
   // apart, whose swizzles put them in distinct banks
   const int rbase = (g & ~7) | ((g >> 1) & 3) | ((g & 1) << 2);
-  const SymDev& S = a.sym;
   const float2* __restrict__ Sd = (const float2*)S.data;
   float2* const node = a.node + slab_off;
   float2* const scr = a.scratch + slab_off;
@@ -182,21 +218,19 @@ __global__ void __launch_bounds__(fz::THREADS, 2) k_fuse2(const FuseArgs a) {
 #pragma unroll 1
     for (int kr = 0; kr < 2; ++kr) {
       const int f1 = rbase + (N / 2) * kr;
-      const int fp0 = 2 * (int)i0 + a.prefix0, fp1 = 2 * f1 + b1;
-      const int clsp = ((fp0 & 1) << 1) | (fp1 & 1);
-      int foldp = 0;
-      int fm = fp0;
-      if (fm > S.n[0]) { fm = 2 * S.n[0] - fm; foldp |= 1; }
-      unsigned lin = (unsigned)(fm >> 1);
-      fm = fp1;
-      if (fm > S.n[1]) { fm = 2 * S.n[1] - fm; foldp |= 2; }
-      lin = lin * (unsigned)S.J[clsp << 1][1] + (unsigned)(fm >> 1);
-      // sign bit k: stored block k read negated (low / folded high frequencies)
+      // the column dim pd: frequency 2 f1 + b1
+      const int pd = a.pd, fp1 = 2 * f1 + b1;
+      const int clsp = (clspp << 1) | (fp1 & 1);
+      int foldp = foldpp, fm = fp1;
+      if (fm > S.n[pd]) { fm = 2 * S.n[pd] - fm; foldp |= 1 << pd; }
+      const unsigned lin = linp * (unsigned)S.J[clsp << 1][pd] + (unsigned)(fm >> 1);
+      // sign bit k: stored block k read negated (low / folded high frequencies
+      // of the row dim pd + 1)
       unsigned sgl = 0, sgh = 0;
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         sgl |= (unsigned)(__popc(S.oddmask[k] & foldp) & 1) << k;
-        sgh |= (unsigned)(__popc(S.oddmask[k] & (foldp | 4)) & 1) << k;
+        sgh |= (unsigned)(__popc(S.oddmask[k] & (foldp | (2 << pd))) & 1) << k;
       }
       // point t + 8 m of row f1 sits at (t + 8 m) xor swz = tt + 8 (m xor s3):
       // one base for even m, one for odd m (+ c N N for component c)
@@ -212,7 +246,7 @@ __global__ void __launch_bounds__(fz::THREADS, 2) k_fuse2(const FuseArgs a) {
 #pragma unroll 1
       for (int b2 = 0; b2 < 2; ++b2) {
         const int cl = (clsp << 1) | b2;
-        const float2* __restrict__ rw = Sd + S.cls_off[cl] + (long long)lin * S.J[cl][2];
+        const float2* __restrict__ rw = Sd + S.cls_off[cl] + (long long)lin * S.J[cl][pd + 1];
         const long long bk = S.blk[cl];
 #pragma unroll
         for (int c = 0; c < 3; ++c) fft64<false>(w[c], t, xv, tw);
@@ -312,11 +346,11 @@ __global__ void __launch_bounds__(fz::THREADS, 2) k_fuse2(const FuseArgs a) {
   }
 }
 
-// d = 3, c = 3 split plan on the compressed block-symmetric store with
-// n_1 = n_2 = 64, complex64.
+// c = 3 split plan, d >= 3, with n_{d-2} = n_{d-1} = 64, on the compressed
+// block-symmetric store, complex64.
 bool fuse2_supported(int d, int c, const int* n, size_t esz, const SymDev& S) {
-  if (d != 3 || c != 3 || esz != sizeof(float2)) return false;
-  if (n[1] != fz::N || n[2] != fz::N) return false;
+  if (d < 3 || d > MAX_D || c != 3 || esz != sizeof(float2)) return false;
+  if (n[d - 2] != fz::N || n[d - 1] != fz::N) return false;
   if (!S.compressed || S.nsym != 6) return false;
   if (S.comp[0][0] != 0 || S.comp[1][1] != 1 || S.comp[2][2] != 2 || S.comp[0][1] != 3 || S.comp[0][2] != 4 ||
       S.comp[1][2] != 5)
@@ -324,19 +358,28 @@ bool fuse2_supported(int d, int c, const int* n, size_t esz, const SymDev& S) {
   return true;
 }
 
-// Errors: cudaErrorInvalidValue for a shape the kernel does not take,
-// cudaErrorMisalignedAddress unless node and scratch are 16-byte aligned.
-cudaError_t launch_fuse2(float2* node, float2* scratch, int prefix0, int n0, int nrhs, const FftDev& f1,
-                         const FftDev& f2, const SymDev& sym, cudaStream_t st) {
-  if (f1.N != fz::N || f2.N != fz::N || n0 < 1 || nrhs < 0) return cudaErrorInvalidValue;
+// node: a level-(d-2) node with parity bits `prefix` (bit m for dim m),
+// scratch: a vector of the same size.  Errors: cudaErrorInvalidValue for a
+// shape the kernel does not take, cudaErrorMisalignedAddress unless node and
+// scratch are 16-byte aligned.
+cudaError_t launch_fuse2(float2* node, float2* scratch, int prefix, int d, const int* n, int nrhs,
+                         const FftDev& f1, const FftDev& f2, const SymDev& sym, cudaStream_t st) {
+  if (d < 3 || d > MAX_D || f1.N != fz::N || f2.N != fz::N || nrhs < 0) return cudaErrorInvalidValue;
   if (((uintptr_t)node | (uintptr_t)scratch) & 15) return cudaErrorMisalignedAddress;
-  const long long blocks = (long long)nrhs * n0;
-  if (blocks == 0) return cudaSuccess;
-  if (blocks >= (1ll << 31)) return cudaErrorInvalidValue;
   FuseArgs a;
   memset(&a, 0, sizeof a);
-  a.node = node; a.scratch = scratch; a.n0 = n0; a.nrhs = nrhs; a.prefix0 = prefix0;
-  a.comp_stride = (long long)n0 * fz::N * fz::N;
+  long long nslab = 1;
+  a.pd = d - 2;
+  for (int m = 0; m < a.pd; ++m) {
+    if (n[m] < 1) return cudaErrorInvalidValue;
+    a.ext[m] = n[m];
+    nslab *= n[m];
+  }
+  const long long blocks = (long long)nrhs * nslab;
+  if (blocks == 0) return cudaSuccess;
+  if (blocks >= (1ll << 31)) return cudaErrorInvalidValue;
+  a.node = node; a.scratch = scratch; a.prefix = prefix; a.nrhs = nrhs; a.nslab = (unsigned)nslab;
+  a.comp_stride = nslab * fz::N * fz::N;
   a.tw = (const float2*)f2.tw; a.ph = (const float2*)f2.ph;
   a.sym = sym;
   cudaError_t e = set_smem_attr<k_fuse2>((int)fz::SMEM);

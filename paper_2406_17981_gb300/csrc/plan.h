@@ -127,11 +127,11 @@ bool two_level_fusable(btmv_plan p);
 // ... and an apply with nrhs right-hand sides into y takes it (grid size and
 // alignment rules of btmv.h).
 bool fuse_this_apply(btmv_plan p, int nrhs, const void* y);
-// The fused last two levels (fused2.cu): d = 3, c = 3, complex64, block-
-// symmetric compressed store, n_1 = n_2 = 64.
+// The fused last two levels (fused2.cu): d >= 3, c = 3, complex64, block-
+// symmetric compressed store, n_{d-2} = n_{d-1} = 64.
 bool fuse2_supported(int d, int c, const int* n, size_t esz, const SymDev& S);
-cudaError_t launch_fuse2(float2* node, float2* scratch, int prefix0, int n0, int nrhs, const FftDev& f1,
-                         const FftDev& f2, const SymDev& sym, cudaStream_t st);
+cudaError_t launch_fuse2(float2* node, float2* scratch, int prefix, int d, const int* n, int nrhs,
+                         const FftDev& f1, const FftDev& f2, const SymDev& sym, cudaStream_t st);
 // The whole apply of a d = 2, c = 1, 64 x 64 split plan as one cluster
 // kernel (small2d.cu); dbl: complex128.
 bool small2d_supported(int d, int c, const int* n, const SymDev& S);

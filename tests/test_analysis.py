@@ -65,6 +65,12 @@ def test_fused_pass_bytes_drop_the_inner_levels():
     assert fused["fwd_split"] + fused["bwd_merge"] == 6 * V
     with pytest.raises(ValueError):
         A.fused_pass_bytes((8, 8), 1, 1, 8, 0)
+    # d = 4: levels 1 and 2 keep their passes (3V + 2 x 3V each way), four
+    # fused nodes move 2V each: 26 V + symbol against 58 V + symbol unfused
+    n4 = (4, 4, 64, 64)
+    V4 = 4 * 4 * 64 * 64 * 3 * 8
+    assert A.fused_pass_bytes(n4, 3, 1, 8, S)["total"] == 26 * V4 + S
+    assert A.split_pass_bytes(n4, 3, 1, 8, S)["total"] == 58 * V4 + S
 
 
 def test_apply_kind_bytes_one_kernel_and_split():

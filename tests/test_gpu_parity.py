@@ -541,7 +541,13 @@ def test_padded_green_parity_and_adjoint(n):
 
 
 FUSED_CASES = [((1, 64, 64), "green", 1), ((3, 64, 64), "green", 2), ((7, 64, 64), "skew", 3),
-               ((16, 64, 64), "green", 1), ((5, 64, 64), "skew", 1)]
+               ((16, 64, 64), "green", 1), ((5, 64, 64), "skew", 1), ((2, 3, 64, 64), "skew", 2),
+               ((3, 1, 64, 64), "skew", 1), ((2, 2, 2, 64, 64), "skew", 1)]
+
+
+def _fused_launches(d):
+    """Forward split + merge per node of levels 0..d-3, one fused launch per level-(d-2) node."""
+    return sum(2 << m for m in range(d - 2)) + (1 << (d - 2))
 
 
 def _fused_instance(n, kind, nrhs):
@@ -559,8 +565,8 @@ def test_fused_two_levels(n, kind, nrhs, streams, monkeypatch):
     """The last two levels of Algorithm 1 as one kernel per level-1 node
     (dim-1 split, leaf along dim 2, dim-1 merge on a shared-memory slab)
     against the FP64 oracle and the unfused schedule, with and without the
-    two-stream traversal; the fused plan launches 4 kernels per apply
-    (fusion forced on these small grids)."""
+    two-stream traversal, d = 3..5; a d = 3 fused plan launches 4 kernels
+    per apply (fusion forced on these small grids)."""
     monkeypatch.setenv("BTMV_FUSE_MIN_BLOCKS", "0")
     t_orth, par, x = _fused_instance(n, kind, nrhs)
     flags = bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY
@@ -573,7 +579,7 @@ def test_fused_two_levels(n, kind, nrhs, streams, monkeypatch):
     plan = bt.Plan(n, 3, 0, max_rhs=nrhs, flags=bt.BTMV_FLAG_FUSED_LEVELS)
     try:
         plan.set_kernel(t_orth, flags, par)
-        assert plan.info["launches_per_apply"] == 4
+        assert plan.info["launches_per_apply"] == _fused_launches(len(n))
     finally:
         plan.close()
 
