@@ -40,6 +40,7 @@
 //
 // Layout: c = 3 on the mirror-compressed block-symmetric store (stored
 // blocks 00 11 22 01 02 12), complex64, N1 = N2 = 64, d >= 3.
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 
@@ -346,6 +347,20 @@ __global__ void __launch_bounds__(fz::THREADS, 2) k_fuse2(const FuseArgs a) {
   }
 }
 
+// Set a function attribute once per device (devices 0..63), as
+// set_smem_attr does for the shared-memory size.
+template <auto K>
+static cudaError_t func_attr_once(cudaFuncAttribute attr, int value) {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(K, attr, value);
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
+
 // c = 3 split plan, d >= 3, with n_{d-2} = n_{d-1} = 64, on the compressed
 // block-symmetric store, complex64.
 bool fuse2_supported(int d, int c, const int* n, size_t esz, const SymDev& S) {
@@ -385,7 +400,7 @@ cudaError_t launch_fuse2(float2* node, float2* scratch, int prefix, int d, const
   cudaError_t e = set_smem_attr<k_fuse2>((int)fz::SMEM);
   if (e != cudaSuccess) return e;
   // all of the unified L1 as shared memory: two blocks of 113 KB per SM
-  e = cudaFuncSetAttribute(k_fuse2, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  e = func_attr_once<k_fuse2>(cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   return launch_pdl(k_fuse2, dim3((unsigned)blocks), dim3(fz::THREADS), fz::SMEM, st, a);
 }

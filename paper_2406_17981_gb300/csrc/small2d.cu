@@ -27,6 +27,7 @@
 // the column phases, where half of the warps idle).
 #include <cooperative_groups.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -207,11 +208,25 @@ bool small2d_supported(int d, int c, const int* n, const SymDev& S) {
   return d == 2 && c == 1 && n[0] == s2::N && n[1] == s2::N && S.nsym == 1 && S.comp[0][0] == 0;
 }
 
+// Set a function attribute once per device (devices 0..63), as
+// set_smem_attr does for the shared-memory size.
+template <auto K>
+static cudaError_t func_attr_once(cudaFuncAttribute attr, int value) {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(K, attr, value);
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
+
 template <class T, int K>
 static cudaError_t small2d_k(const Small2dArgs& a, int nrhs, cudaStream_t st) {
   typedef Small2dCfg<T, K> CF;
   cudaError_t e = cudaSuccess;
-  if (K > 8) e = cudaFuncSetAttribute(k_small2d<T, K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (K > 8) e = func_attr_once<k_small2d<T, K>>(cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   if (CF::SMEM > 48 * 1024) e = set_smem_attr<k_small2d<T, K>>((int)CF::SMEM);
   if (e != cudaSuccess) return e;
