@@ -122,8 +122,10 @@ enum {
                                       in shared memory (Sec. II.B); other
                                       plans ignore the flag.  An apply fuses
                                       when its grid has at least 4 blocks per
-                                      SM (nrhs n_1 .. n_{d-2} >= 4 x SMs;
-                                      BTMV_FUSE_MIN_BLOCKS=k in the
+                                      SM (nrhs n_1 .. n_{d-2} >= 4 x SMs, 2 x
+                                      SMs with BTMV_FLAG_TWO_STREAMS, whose
+                                      two subtrees' launches run side by
+                                      side; BTMV_FUSE_MIN_BLOCKS=k in the
                                       environment sets k), else it runs
                                       unfused; plan info counts launches for
                                       max_rhs                                 */

@@ -804,18 +804,21 @@ bool btmv::two_level_fusable(btmv_plan p) {
   return fuse2_supported(p->d, p->c, p->n, sizeof(float2), p->symdev);
 }
 
-// The fused kernel runs one block per (dim-0 index, right-hand side) and
+// The fused kernel runs one block per (prefix index, right-hand side) and
 // measured slower than the unfused schedule on small grids (64^3 with one
 // right-hand side, 64 blocks: 0.116 against 0.071 ms), level at 512 blocks
 // and 9-13% faster from 1024 blocks (two blocks per SM), so an apply fuses
-// from 4 blocks per SM; BTMV_FUSE_MIN_BLOCKS=k in the environment sets
-// another threshold (0: always).  The kernel copies the node it updates in
+// from 4 blocks per SM; with the two-stream traversal the two subtrees'
+// fused launches run side by side, and 512 blocks each measured faster
+// (64^3, 8 right-hand sides: 0.338 against 0.362 ms), so from 2 blocks per
+// SM there.  BTMV_FUSE_MIN_BLOCKS=k in the environment sets another
+// threshold (0: always).  The kernel copies the node it updates in
 // 16-byte pieces; btmv_apply already requires 16-byte aligned x and y, and
 // the test below keeps any other caller unfused.
 static long long fuse_min_blocks(btmv_plan p) {
   const char* v = getenv("BTMV_FUSE_MIN_BLOCKS");
   if (v && *v) return atoll(v);
-  return 4ll * std::max(1, p->nsm);
+  return (p->side ? 2ll : 4ll) * std::max(1, p->nsm);
 }
 
 // blocks of one fused launch: one per prefix index and right-hand side

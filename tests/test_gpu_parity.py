@@ -630,9 +630,10 @@ def test_fused_two_levels_profile(monkeypatch):
 
 
 def test_fused_two_levels_grid_threshold(monkeypatch):
-    """By default an apply fuses from 4 blocks per SM (nrhs n_0 >= 4 x SMs):
-    on (76, 64, 64) eight right-hand sides fuse and one does not, and both
-    results match the oracle."""
+    """By default an apply fuses from 4 blocks per SM (nrhs n_0 >= 4 x SMs),
+    2 with the two-stream traversal: on (76, 64, 64) eight right-hand sides
+    fuse and one does not, on (38, 64, 64) eight fuse only with two streams,
+    and every result matches the oracle."""
     monkeypatch.delenv("BTMV_FUSE_MIN_BLOCKS", raising=False)
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     n0 = -(-4 * nsm // 8)
@@ -658,6 +659,24 @@ def test_fused_two_levels_grid_threshold(monkeypatch):
         assert rel(y1.cpu().numpy().astype(np.complex128), ref[:1]) <= 1e-5
     finally:
         plan.close()
+    # half the grid: unfused on one stream, fused with the two-stream traversal
+    n2 = (-(-2 * nsm // 8), 64, 64)
+    t2, par2 = W.green_dyadic_orthant(n2, kh=W.KH_GREEN)
+    x2 = W.random_vector(n2, 3, seed=100, nrhs=r)
+    ref2 = OE.embed_matvec(W.orthant_to_full(t2, par2), round_input(x2, 0))
+    x2d = torch.from_numpy(np.ascontiguousarray(x2.astype(np.complex64))).cuda()
+    for extra, fused in ((0, False), (bt.BTMV_FLAG_TWO_STREAMS, True)):
+        plan = bt.Plan(n2, 3, 0, max_rhs=r, flags=bt.BTMV_FLAG_FUSED_LEVELS | bt.BTMV_FLAG_PROFILE | extra)
+        try:
+            plan.set_kernel(t2, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par2)
+            y2 = torch.zeros_like(x2d)
+            bt.btmv_profile_read(plan.handle)
+            plan.apply(x2d, y2, r)
+            prof = bt.btmv_profile_read(plan.handle)
+            assert (prof["fused_levels"][1] == 2) == fused
+            assert rel(y2.cpu().numpy().astype(np.complex128), ref2) <= 1e-5
+        finally:
+            plan.close()
 
 
 SMALL2D_CASES = [("random", 0, 1), ("random", 1, 3), ("green", 0, 2), ("green", 1, 1), ("skew", 1, 2),
