@@ -391,7 +391,8 @@ enum {
   BTMV_K_FULL_LEAF = 4,    /* full embedding: last-dim forward+multiply+inverse */
   BTMV_K_FULL_INV = 5,     /* full embedding: inverse passes (+ projection)    */
   BTMV_K_COPY = 6,         /* host staging copies                              */
-  BTMV_K_FUSED_LEVELS = 7, /* two fused levels (BTMV_FLAG_FUSED_LEVELS)       */
+  BTMV_K_FUSED_LEVELS = 7, /* last two levels in one kernel: BTMV_FLAG_FUSED_LEVELS
+                              launches, and the one-launch d = 2 apply         */
   BTMV_K_NKINDS = 8
 };
 
