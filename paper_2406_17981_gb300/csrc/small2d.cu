@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(Small2dCfg<T, K>::THREADS) k_small2d(const Sma
   const Xb<T> xv{xbuf + g * N, (g & 1) << 3};
   __syncthreads();
   cluster.sync();                                  // every CTA of the cluster is running
+  grid_dep_wait();                                 // x and y of the previous kernel on the stream
 
   // 1: column i1 of child b0, forward along dim 0, each value sent to the owner
   // of its row (groups g < L; the others idle as whole warps)
@@ -235,13 +236,17 @@ static cudaError_t small2d_k(const Small2dArgs& a, int nrhs, cudaStream_t st) {
   cfg.blockDim = dim3(CF::THREADS);
   cfg.dynamicSmemBytes = CF::SMEM;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  // programmatic dependent launch: the prologue (tables, the first cluster
+  // barrier) runs while the previous kernel of the stream retires
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = K;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_small2d<T, K>, a);
 }
 
