@@ -257,13 +257,11 @@ static cudaError_t small2d_k(const Small2dArgs& a, int nrhs, cudaStream_t st) {
 template <class T>
 static cudaError_t small2d_t(const Small2dArgs& a, int nrhs, cudaStream_t st) {
   if (nrhs < 1) return cudaErrorInvalidValue;
-  static int k16[64] = {0};                        // per device: 0 unknown, 1 yes, 2 no
+  static std::atomic<int> k16[64];                 // per device: 0 unknown, 1 yes, 2 no
   int dev = 0;
   cudaGetDevice(&dev);
-  int& ok16 = k16[dev & 63];
   const char* force = getenv("BTMV_SMALL2D_CLUSTER");
-  int forced = (force && force[0] == '8') ? 2 : 0;
-  int& ok = forced ? forced : ok16;
+  int ok = (force && force[0] == '8') ? 2 : k16[dev & 63].load(std::memory_order_relaxed);
   if (ok == 0) {
     typedef Small2dCfg<T, 16> CF;
     int maxc = 0;
@@ -282,6 +280,7 @@ static cudaError_t small2d_t(const Small2dArgs& a, int nrhs, cudaStream_t st) {
                       cudaSuccess;
     ok = (attr && cudaOccupancyMaxActiveClusters(&maxc, k_small2d<T, 16>, &cfg) == cudaSuccess && maxc > 0) ? 1 : 2;
     cudaGetLastError();
+    k16[dev & 63].store(ok, std::memory_order_relaxed);
   }
   constexpr int YMAX = 65535;
   for (int q0 = 0; q0 < nrhs; q0 += YMAX) {
