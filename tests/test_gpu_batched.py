@@ -216,3 +216,34 @@ def test_each_batched_execution_mode(mode, monkeypatch):
     finally:
         for p in plans:
             p.close()
+
+
+def test_batched_plans_with_fused_or_one_launch_applies(monkeypatch):
+    """Plans whose own btmv_apply takes a fused form -- the last two levels
+    in one kernel (BTMV_FLAG_FUSED_LEVELS, forced on a small grid) and the
+    one-launch d = 2 apply -- run the plain schedule inside a batch; every
+    problem of the batch still matches the FP64 oracle."""
+    monkeypatch.setenv("BTMV_FUSE_MIN_BLOCKS", "0")
+    specs = []
+    n3 = (3, 64, 64)
+    t3, par3 = W.green_dyadic_orthant(n3, kh=W.KH_GREEN)
+    p3 = bt.Plan(n3, 3, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=2, flags=bt.BTMV_FLAG_FUSED_LEVELS)
+    p3.set_kernel(t3, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par3)
+    specs.append((p3, W.random_vector(n3, 3, seed=71, nrhs=2), W.orthant_to_full(t3, par3)))
+    n2 = (64, 64)
+    t2 = W.random_generator(n2, 1, seed=72)
+    p2 = bt.Plan(n2, 1, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=3)
+    p2.set_kernel(t2)
+    assert p2.info["launches_per_apply"] == 1
+    specs.append((p2, W.random_vector(n2, 1, seed=73, nrhs=3), t2))
+    try:
+        xs = [torch.from_numpy(x.astype(np.complex64)).cuda() for _, x, _ in specs]
+        ys = [torch.zeros_like(x) for x in xs]
+        bt.btmv_apply_batched([p.handle for p, _, _ in specs], xs, ys, [x.shape[0] for x in xs])
+        torch.cuda.synchronize()
+        for (p, x, tf), yd in zip(specs, ys):
+            ref = OE.embed_matvec(tf, round_input(x, 0))
+            assert rel(yd.cpu().numpy().astype(np.complex128), ref) <= 1e-5
+    finally:
+        for p, _, _ in specs:
+            p.close()

@@ -138,3 +138,31 @@ def test_noalloc_success_clears_an_earlier_error():
         assert bt.btmv_last_error() == ""
     finally:
         plan.close()
+
+
+def test_noalloc_on_the_fused_and_one_launch_paths(monkeypatch):
+    """The staged apply also takes the fused forms btmv_apply takes -- the
+    last two levels in one kernel (BTMV_FLAG_FUSED_LEVELS, forced here) and
+    the one-launch d = 2 apply -- and matches btmv_apply on two calls in a
+    row."""
+    monkeypatch.setenv("BTMV_FUSE_MIN_BLOCKS", "0")
+    cases = []
+    n3 = (2, 64, 64)
+    t3, par3 = W.green_dyadic_orthant(n3, kh=W.KH_GREEN)
+    p3 = bt.Plan(n3, 3, bt.BTMV_C64, bt.BTMV_ALGO_SPLIT, max_rhs=1, flags=bt.BTMV_FLAG_FUSED_LEVELS)
+    p3.set_kernel(t3, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par3)
+    cases.append((p3, n3, 3, np.complex64, 1e-6))
+    n2 = (64, 64)
+    p2 = bt.Plan(n2, 1, bt.BTMV_C128, bt.BTMV_ALGO_SPLIT, max_rhs=1)
+    p2.set_kernel(W.random_generator(n2, 1, seed=74))
+    cases.append((p2, n2, 1, np.complex128, 1e-13))
+    try:
+        for plan, n, c, dt, tol in cases:
+            for call in range(2):
+                x = np.ascontiguousarray(W.random_vector(n, c, seed=75 + call, nrhs=1).astype(dt))
+                y = np.zeros_like(x)
+                bt.btmv_apply_host_noalloc(plan.handle, x, y, 1)
+                assert rel(y.astype(np.complex128), _device_apply(plan, x).astype(np.complex128)) <= tol
+    finally:
+        for plan, *_ in cases:
+            plan.close()
