@@ -483,10 +483,11 @@ def measure_single(args, cfg, ws, rank, local):
 
 def compact_single(args, workload, steps):
     """One single-problem workload in brief: split matvecs/s over `steps`
-    applies (inputs rotated past L2), the dominant kernel's roofline, and the
-    error against the FP64 oracle (the full circulant embedding up to 128^3,
-    the direct sum at 8 sampled points above, the dense direct sum for the
-    64^2 complex128 configuration)."""
+    applies (inputs rotated past L2), the dominant kernel's roofline, the
+    two-stream traversal's rate for d >= 3, and the error against the FP64
+    oracle (the full circulant embedding up to 128^3, the direct sum at 8
+    sampled points above, the dense direct sum for the 64^2 complex128
+    configuration)."""
     import torch
 
     from paper_2406_17981_gb300 import analysis as A
@@ -536,6 +537,9 @@ def compact_single(args, workload, steps):
            "kernels": kernels, "launches_per_step": info["launches_per_apply"]}
     y = ys[(steps - 1) % npool].cpu().numpy().astype(np.complex128)
     plan.close()
+    if len(n) >= 3:
+        # the same apply with the two top-level subtrees on two streams
+        out["two_stream_variant"] = time_two_streams(args, cfg, t, par, sflags, xc, prec, V)
     if not args.no_cpu:
         tf = W.orthant_to_full(t, par) if par is not None else t
         x128 = xc.astype(np.complex128)
