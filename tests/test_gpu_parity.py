@@ -542,7 +542,7 @@ def test_padded_green_parity_and_adjoint(n):
 
 FUSED_CASES = [((1, 64, 64), "green", 1), ((3, 64, 64), "green", 2), ((7, 64, 64), "skew", 3),
                ((16, 64, 64), "green", 1), ((5, 64, 64), "skew", 1), ((2, 3, 64, 64), "skew", 2),
-               ((3, 1, 64, 64), "skew", 1), ((2, 2, 2, 64, 64), "skew", 1)]
+               ((3, 1, 64, 64), "skew", 1), ((2, 2, 2, 64, 64), "skew", 1), ((11, 64, 64), "green", 2)]
 
 
 def _fused_launches(d):
