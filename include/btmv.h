@@ -128,7 +128,10 @@ enum {
                                       side; BTMV_FUSE_MIN_BLOCKS=k in the
                                       environment sets k), else it runs
                                       unfused; plan info counts launches for
-                                      max_rhs                                 */
+                                      max_rhs.  Trailing sizes 128 x 128 take
+                                      a 16-CTA cluster per slab only with
+                                      BTMV_FUSE_CLUSTER=1 in the environment
+                                      (measured slower than unfused)          */
 };
 
 /*

@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libbtmv.so")
 
 SOURCES = ["btmv.cu", "kernels.cu", "persistent.cu", "fast_pass.cu", "fast_leaf.cu", "batch.cu", "noalloc.cu",
            "hostpipe.cu", "cufft_full.cu", "fast_leaf3.cu", "fast_pass_tma.cu", "fused2.cu",
-           "small2d.cu"]
+           "small2d.cu", "fused2c.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

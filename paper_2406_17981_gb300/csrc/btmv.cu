@@ -801,8 +801,17 @@ static void split_children(btmv_plan p, int m, void* e, void* o, int pe, int po,
 
 bool btmv::two_level_fusable(btmv_plan p) {
   if (!(p->flags & BTMV_FLAG_FUSED_LEVELS) || p->algo != BTMV_ALGO_SPLIT || p->prec != BTMV_C64) return false;
-  return fuse2_supported(p->d, p->c, p->n, sizeof(float2), p->symdev);
+  if (fuse2_supported(p->d, p->c, p->n, sizeof(float2), p->symdev)) return true;
+  // 128 x 128 slabs (one 16-CTA cluster per slab) measured 4x slower than the
+  // unfused schedule at 128^3 (1468 against 373 us per apply), so that form
+  // is taken only with BTMV_FUSE_CLUSTER=1 in the environment
+  const char* v = getenv("BTMV_FUSE_CLUSTER");
+  if (!v || v[0] != '1') return false;
+  return fuse2c_supported(p->d, p->c, p->n, sizeof(float2), p->symdev) && fuse2c_available();
 }
+
+// 128 x 128 slabs take the cluster kernel (16 CTAs per slab)
+static bool fuse_cluster_form(btmv_plan p) { return p->n[p->d - 1] == 128; }
 
 // The fused kernel runs one block per (prefix index, right-hand side) and
 // measured slower than the unfused schedule on small grids (64^3 with one
@@ -821,16 +830,19 @@ static long long fuse_min_blocks(btmv_plan p) {
   return (p->side ? 2ll : 4ll) * std::max(1, p->nsm);
 }
 
-// blocks of one fused launch: one per prefix index and right-hand side
+// CTAs of one fused launch: one per prefix index and right-hand side (16
+// per slab for the cluster form, whose grid takes at most 65535 slabs)
 static long long fuse_blocks(btmv_plan p, int nrhs) {
   long long b = nrhs;
   for (int m = 0; m + 2 < p->d; ++m) b *= p->n[m];
+  if (fuse_cluster_form(p)) return b > 65535 ? 0 : 16 * b;
   return b;
 }
 
 bool btmv::fuse_this_apply(btmv_plan p, int nrhs, const void* y) {
   if (!two_level_fusable(p) || ((uintptr_t)y & 15)) return false;
-  return fuse_blocks(p, nrhs) >= fuse_min_blocks(p);
+  const long long b = fuse_blocks(p, nrhs);
+  return b > 0 && b >= fuse_min_blocks(p);
 }
 
 void btmv::split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& out, bool fuse) {
@@ -851,8 +863,11 @@ void btmv::split_steps(btmv_plan p, const void* x, void* y, std::vector<Step>& o
 static btmv_status fused_levels(btmv_plan p, const Step& s, int nrhs, cudaStream_t st) {
   ProfScope ps(p, BTMV_K_FUSED_LEVELS, st);
   const int m = s.dim;
-  cudaError_t e = launch_fuse2((float2*)s.out0, (float2*)s.out1, s.nodes[0].prefix, p->d, p->n, nrhs,
-                               p->fft_apply[m], p->fft_apply[m + 1], p->symdev, st);
+  cudaError_t e = fuse_cluster_form(p)
+      ? launch_fuse2c((float2*)s.out0, (float2*)s.out1, s.nodes[0].prefix, p->d, p->n, nrhs, p->fft_apply[m],
+                      p->fft_apply[m + 1], p->symdev, st)
+      : launch_fuse2((float2*)s.out0, (float2*)s.out1, s.nodes[0].prefix, p->d, p->n, nrhs, p->fft_apply[m],
+                     p->fft_apply[m + 1], p->symdev, st);
   if (e != cudaSuccess) return fail(BTMV_E_CUDA, "fused levels: %s", cudaGetErrorString(e));
   return BTMV_OK;
 }
@@ -1133,7 +1148,7 @@ static int launches_per_apply(btmv_plan p) {
   if (p->algo == BTMV_ALGO_SPLIT) {
     if (d == 1 || use_small2d(p)) return 1;
     int n = 0;
-    if (two_level_fusable(p) && fuse_blocks(p, p->max_rhs) >= fuse_min_blocks(p)) {
+    if (two_level_fusable(p) && fuse_blocks(p, p->max_rhs) > 0 && fuse_blocks(p, p->max_rhs) >= fuse_min_blocks(p)) {
       // forward + merge per node of levels 0..d-3, one fused launch per level-(d-2) node
       for (int m = 0; m < d - 2; ++m) n += 2 * (1 << m);
       return n + (1 << (d - 2));

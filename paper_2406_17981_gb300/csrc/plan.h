@@ -132,6 +132,13 @@ bool fuse_this_apply(btmv_plan p, int nrhs, const void* y);
 bool fuse2_supported(int d, int c, const int* n, size_t esz, const SymDev& S);
 cudaError_t launch_fuse2(float2* node, float2* scratch, int prefix, int d, const int* n, int nrhs,
                          const FftDev& f1, const FftDev& f2, const SymDev& sym, cudaStream_t st);
+// The same for n_{d-2} = n_{d-1} = 128 on a 16-CTA cluster per slab
+// (fused2c.cu); available: the current device schedules that cluster.
+bool fuse2c_supported(int d, int c, const int* n, size_t esz, const SymDev& S);
+bool fuse2c_available();
+long long fuse2c_clusters(int d, const int* n, int nrhs);
+cudaError_t launch_fuse2c(float2* node, float2* scratch, int prefix, int d, const int* n, int nrhs,
+                          const FftDev& f1, const FftDev& f2, const SymDev& sym, cudaStream_t st);
 // The whole apply of a d = 2, c = 1, 64 x 64 split plan as one cluster
 // kernel (small2d.cu); dbl: complex128.
 bool small2d_supported(int d, int c, const int* n, const SymDev& S);

@@ -763,3 +763,53 @@ def test_small_two_level_more_rhs_than_one_grid_dimension(monkeypatch):
     a = ys["1"][idx].cpu().numpy().astype(np.complex128)
     b = ys["0"][idx].cpu().numpy().astype(np.complex128)
     assert rel(a, b) <= 1e-6
+
+
+FUSED128_CASES = [((4, 128, 128), "green", 1), ((3, 128, 128), "skew", 2), ((2, 2, 128, 128), "skew", 1)]
+
+
+@pytest.mark.parametrize("n,kind,nrhs", FUSED128_CASES)
+@pytest.mark.parametrize("streams", [0, 1])
+def test_fused_two_levels_cluster_128(n, kind, nrhs, streams, monkeypatch):
+    """The last two levels fused for 128 x 128 slabs, one 16-CTA cluster per
+    slab exchanging columns and rows through distributed shared memory,
+    against the FP64 oracle and the unfused schedule.  The form is opt-in
+    (BTMV_FUSE_CLUSTER=1; it measured slower than the unfused schedule), and
+    fusion is forced on these small grids."""
+    monkeypatch.setenv("BTMV_FUSE_MIN_BLOCKS", "0")
+    monkeypatch.setenv("BTMV_FUSE_CLUSTER", "1")
+    t_orth, par, x = _fused_instance(n, kind, nrhs)
+    flags = bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY
+    extra = bt.BTMV_FLAG_TWO_STREAMS if streams else 0
+    ref = OE.embed_matvec(W.orthant_to_full(t_orth, par), round_input(x, 0))
+    y0 = run_btmv(t_orth, x, n, 3, 0, 0, flags, par, flags=extra)
+    y1 = run_btmv(t_orth, x, n, 3, 0, 0, flags, par, flags=extra | bt.BTMV_FLAG_FUSED_LEVELS)
+    assert rel(y1, ref) <= 1e-5
+    assert rel(y1, y0) <= 1e-6
+    plan = bt.Plan(n, 3, 0, max_rhs=nrhs, flags=bt.BTMV_FLAG_FUSED_LEVELS | bt.BTMV_FLAG_PROFILE)
+    try:
+        plan.set_kernel(t_orth, flags, par)
+        assert plan.info["launches_per_apply"] == _fused_launches(len(n))
+        xd = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+        yd = torch.zeros_like(xd)
+        bt.btmv_profile_read(plan.handle)
+        plan.apply(xd, yd, nrhs)
+        prof = bt.btmv_profile_read(plan.handle)
+        assert prof["fused_levels"][1] == 1 << (len(n) - 2) and prof["leaf"][1] == 0
+    finally:
+        plan.close()
+
+
+def test_fused_flag_leaves_128_slabs_unfused_by_default(monkeypatch):
+    """Without BTMV_FUSE_CLUSTER=1 a 128 x 128-slab plan under
+    BTMV_FLAG_FUSED_LEVELS runs the unfused schedule."""
+    monkeypatch.setenv("BTMV_FUSE_MIN_BLOCKS", "0")
+    monkeypatch.delenv("BTMV_FUSE_CLUSTER", raising=False)
+    n = (2, 128, 128)
+    t_orth, par, x = _fused_instance(n, "green", 1)
+    plan = bt.Plan(n, 3, 0, max_rhs=1, flags=bt.BTMV_FLAG_FUSED_LEVELS)
+    try:
+        plan.set_kernel(t_orth, bt.BTMV_SYM_BLOCK | bt.BTMV_SYM_PARITY, par)
+        assert plan.info["launches_per_apply"] == 8
+    finally:
+        plan.close()
