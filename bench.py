@@ -91,6 +91,7 @@ KERNEL_SOURCES = {
     "merge": ["fast_pass.cu", "fast_pass_tma.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
     "fused2": ["fused2.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
     "small2d": ["small2d.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
+    "fused2c": ["fused2c.cu", "fast.cuh", "kernels.cuh", "fft.cuh"],
 }
 
 
